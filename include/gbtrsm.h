@@ -1,0 +1,157 @@
+/*
+ * gbtrsm -- GB300 (sm_103a) triangular solver with many right-hand sides.
+ *
+ * The operation is the triangular system solver of arXiv 2305.19917
+ * (Section IV: L x = b for a dense lower-triangular L, extended there to n
+ * right-hand sides with the same L), exposed with the BLAS ?trsm forms:
+ *
+ *     side = GB_LEFT :  op(A) * X = alpha * B     A is m x m, B is m x n
+ *     side = GB_RIGHT:  X * op(A) = alpha * B     A is n x n, B is m x n
+ *
+ * op(A) = A (GB_NOTRANS) or A^T (GB_TRANS); A is lower (GB_LOWER) or upper
+ * (GB_UPPER) triangular; with GB_UNIT the diagonal is taken as 1 and not
+ * read.  Only the triangle named by uplo is read.  X overwrites B.
+ *
+ * The solve is carried out by the decompositions of Section V: a diagonal
+ * block solve (the paper's TS task) plus off-diagonal GEMM updates
+ * B2 -= A21 * X1 (the paper's gemm task), arranged as the recursive
+ * (Section V-A), iterative (Section V-B) or blocked (Section V-C) model.
+ *
+ * Conventions common to every entry point
+ *   - Matrices are column-major: element (i, j) of A is A[i + j*lda].
+ *   - A, B (and every other array unless stated) are DEVICE pointers owned
+ *     by the caller; the library never frees them.  Work space the library
+ *     needs is taken from the stream-ordered allocator on `stream` and
+ *     returned before the call's work completes.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated.
+ *   - Status codes: 0 = success; -i = argument i (1-based) is invalid,
+ *     nothing was launched; GB_STATUS_* below for run-time conditions.
+ *   - Quick returns: m == 0 or n == 0 returns 0 and touches nothing.
+ *     alpha == 0 sets B to zero and does not read A (BLAS convention).
+ *   - A zero on a non-unit diagonal is not checked (BLAS convention): the
+ *     result then holds Inf/NaN.
+ *   - The device that owns the pointers must be the current device.
+ */
+#ifndef GBTRSM_H
+#define GBTRSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { GB_LEFT = 0, GB_RIGHT = 1 };
+enum { GB_LOWER = 0, GB_UPPER = 1 };
+enum { GB_NOTRANS = 0, GB_TRANS = 1 };
+enum { GB_NONUNIT = 0, GB_UNIT = 1 };
+
+/* Run-time status codes (positive). */
+enum {
+    GB_STATUS_OK = 0,
+    GB_STATUS_NOT_CONVERGED = 1, /* refinement stopped before reaching tol  */
+    GB_STATUS_CUDA_ERROR = 2,    /* a CUDA call failed; see gb_last_cuda_error */
+    GB_STATUS_TIMEOUT = 3,       /* a device-side wait hit its iteration cap */
+    GB_STATUS_NO_MODEL = 4       /* no cost model loaded where one is needed */
+};
+
+/* Decomposition drivers (the paper's three computation models). */
+enum {
+    GB_DRIVER_BLOCKED = 0,   /* Section V-C: r = ceil(k/nb) diagonal blocks,
+                                one trailing GEMM per block column          */
+    GB_DRIVER_RECURSIVE = 1, /* Section V-A: halve to `depth` levels (refinement
+                                level r = 2^depth), leaves solved blocked    */
+    GB_DRIVER_ITERATIVE = 2, /* Section V-B: fixed block size; block row j is
+                                updated by one GEMM with all solved blocks
+                                0..j-1 (left-looking), then solved           */
+    GB_DRIVER_AUTO = -1      /* let the planner choose                       */
+};
+
+/* Execution plan for one solve.  nb in {16, 32, 64, 128, 256, 512};
+ * depth in 0..12 (recursive driver only). */
+typedef struct gb_plan {
+    int32_t driver;
+    int32_t nb;
+    int32_t depth;
+    int32_t reserved; /* must be 0 */
+} gb_plan;
+
+/*
+ * gb_dtrsm / gb_strsm: FP64 / FP32 triangular solve, X overwrites B.
+ * Arguments (1-based numbers are the ones a negative status refers to):
+ *   1 side, 2 uplo, 3 trans, 4 diag       enum values above
+ *   5 m, 6 n                              rows / columns of B (>= 0)
+ *   7 alpha                               scalar on B
+ *   8 A   device, k x k with k = m (Left) or n (Right); may be NULL only
+ *         when alpha == 0 or m*n == 0
+ *   9 lda >= max(1, k)
+ *  10 B   device, m x n, overwritten by X; may be NULL only when m*n == 0
+ *  11 ldb >= max(1, m)
+ *  12 stream
+ * The plan is picked by the planner (cost model if loaded, else the
+ * built-in default).  Asynchronous.
+ */
+int gb_dtrsm(int side, int uplo, int trans, int diag, int64_t m, int64_t n,
+             double alpha, const double *A, int64_t lda, double *B,
+             int64_t ldb, void *stream);
+int gb_strsm(int side, int uplo, int trans, int diag, int64_t m, int64_t n,
+             float alpha, const float *A, int64_t lda, float *B, int64_t ldb,
+             void *stream);
+
+/*
+ * gb_dtrsm_plan / gb_strsm_plan: as above with an explicit plan
+ * (argument 12, host pointer; NULL = planner's choice); stream is argument
+ * 13.  A plan with an unknown driver, nb outside the set above, depth out of
+ * range or reserved != 0 returns -12.
+ */
+int gb_dtrsm_plan(int side, int uplo, int trans, int diag, int64_t m,
+                  int64_t n, double alpha, const double *A, int64_t lda,
+                  double *B, int64_t ldb, const gb_plan *plan, void *stream);
+int gb_strsm_plan(int side, int uplo, int trans, int diag, int64_t m,
+                  int64_t n, float alpha, const float *A, int64_t lda,
+                  float *B, int64_t ldb, const gb_plan *plan, void *stream);
+
+/*
+ * gb_plan_counts: host-only description of the launches a plan issues for a
+ * triangle of order k (no GPU work).  Writes the number of diagonal-block
+ * solves and of GEMM updates, and the sum over GEMMs of M*N*K / ncols (i.e.
+ * the GEMM multiply-adds per right-hand side).  This exposes the task counts
+ * of the paper's Section V models: 2^j GEMMs at recursion level j
+ * (Section V-A), r(r-1)/2 off-diagonal blocks for r diagonal blocks
+ * (Section V-C; r - 1 launches, one per block column).
+ * Returns 0, or -1 for an invalid plan, -2 for k < 0.
+ */
+int gb_plan_counts(const gb_plan *plan, int64_t k, int64_t *n_diag,
+                   int64_t *n_gemm, int64_t *n_offdiag_blocks,
+                   double *gemm_madds_per_col);
+
+/*
+ * Launch accounting (host only, no GPU work).
+ * gb_kernel_launches: number of kernels this library has launched in the
+ * process so far.
+ * gb_profile_enable(on): clear the per-launch records; while on, every
+ * launch is bracketed by CUDA events on its stream.
+ * gb_profile_read(kind, ...): for kernel kind 0 diagonal solve, 1 CUDA-core
+ * GEMM update, 2 tensor-core GEMM update, 3 split residual, 4 conversion /
+ * elementwise, 5 batched solve, 6 cost-model network: the number of
+ * recorded launches, their summed device time in ms and their summed
+ * algorithmic flops and bytes.  Waits for the recorded events.  Returns 0,
+ * -1 for an unknown kind, GB_STATUS_CUDA_ERROR if an event failed.
+ */
+uint64_t gb_kernel_launches(void);
+int gb_profile_enable(int on);
+int gb_profile_read(int kind, int64_t *launches, double *ms, double *flops,
+                    double *bytes);
+
+/* Message for a status code (static storage). */
+const char *gb_status_string(int status);
+/* Last CUDA error code seen by the library on this host thread (0 = none). */
+int gb_last_cuda_error(void);
+/* Library version as major*10000 + minor*100 + patch. */
+int gb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBTRSM_H */

@@ -1,0 +1,202 @@
+"""Thin ctypes binding of libgbtrsm.so (argument marshalling only).
+
+Functions named ``gb_*`` mirror the C entry points of include/gbtrsm.h one to
+one and take raw device pointers (ints) and a stream handle (int, 0 = legacy
+default stream).  ``trsm`` / ``trsm_plan`` are conveniences that take torch
+CUDA tensors in column-major layout (``stride(0) == 1``) and pass their
+pointers and leading dimensions.  Every computation runs in the CUDA
+library; there is no CPU path, and loading fails loudly if the library has
+not been built.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+LEFT, RIGHT = 0, 1
+LOWER, UPPER = 0, 1
+NOTRANS, TRANS = 0, 1
+NONUNIT, UNIT = 0, 1
+DRIVER_BLOCKED, DRIVER_RECURSIVE, DRIVER_ITERATIVE, DRIVER_AUTO = 0, 1, 2, -1
+STATUS_OK, STATUS_NOT_CONVERGED, STATUS_CUDA_ERROR, STATUS_TIMEOUT, STATUS_NO_MODEL = 0, 1, 2, 3, 4
+
+LIB_PATH = _build.LIB
+
+
+class GbPlan(ctypes.Structure):
+    _fields_ = [("driver", ctypes.c_int32), ("nb", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class GbError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__(f"{fn} returned {status}: {status_string(status)}"
+                         + (f" (cuda error {gb_last_cuda_error()})" if status == STATUS_CUDA_ERROR else ""))
+
+
+_lib = None
+i32, i64, dbl, flt, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_float, ctypes.c_void_p
+
+_SIGS = {
+    "gb_dtrsm": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, vp], i32),
+    "gb_strsm": ([i32, i32, i32, i32, i64, i64, flt, vp, i64, vp, i64, vp], i32),
+    "gb_dtrsm_plan": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, ctypes.POINTER(GbPlan), vp], i32),
+    "gb_strsm_plan": ([i32, i32, i32, i32, i64, i64, flt, vp, i64, vp, i64, ctypes.POINTER(GbPlan), vp], i32),
+    "gb_plan_counts": ([ctypes.POINTER(GbPlan), i64, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                        ctypes.POINTER(i64), ctypes.POINTER(dbl)], i32),
+    "gb_status_string": ([i32], ctypes.c_char_p),
+    "gb_last_cuda_error": ([], i32),
+    "gb_version": ([], i32),
+    "gb_kernel_launches": ([], ctypes.c_uint64),
+    "gb_profile_enable": ([i32], i32),
+    "gb_profile_read": ([i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                         ctypes.POINTER(dbl)], i32),
+}
+
+
+def lib():
+    """Load libgbtrsm.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(l, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = l
+    return _lib
+
+
+def _plan_ptr(plan):
+    if plan is None:
+        return None
+    if isinstance(plan, GbPlan):
+        return ctypes.byref(plan)
+    d = dict(plan)
+    return ctypes.byref(GbPlan(d.get("driver", 0), d.get("nb", 64), d.get("depth", 0), d.get("reserved", 0)))
+
+
+# ---- one-to-one C entry points ------------------------------------------------
+
+def gb_dtrsm(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream=0):
+    return lib().gb_dtrsm(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream or None)
+
+
+def gb_strsm(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream=0):
+    return lib().gb_strsm(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream or None)
+
+
+def gb_dtrsm_plan(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, plan, stream=0):
+    return lib().gb_dtrsm_plan(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb,
+                               _plan_ptr(plan), stream or None)
+
+
+def gb_strsm_plan(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, plan, stream=0):
+    return lib().gb_strsm_plan(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb,
+                               _plan_ptr(plan), stream or None)
+
+
+def gb_plan_counts(plan, k):
+    nd, ng, nbk, md = i64(), i64(), i64(), dbl()
+    st = lib().gb_plan_counts(_plan_ptr(plan), k, ctypes.byref(nd), ctypes.byref(ng),
+                              ctypes.byref(nbk), ctypes.byref(md))
+    if st != 0:
+        raise GbError("gb_plan_counts", st)
+    return dict(n_diag=nd.value, n_gemm=ng.value, n_offdiag_blocks=nbk.value,
+                gemm_madds_per_col=md.value)
+
+
+def gb_status_string(status):
+    return lib().gb_status_string(status).decode()
+
+
+status_string = gb_status_string
+
+
+def gb_last_cuda_error():
+    return lib().gb_last_cuda_error()
+
+
+def gb_version():
+    return lib().gb_version()
+
+
+KERNEL_KINDS = ["diag", "gemm_simt", "gemm_tc", "residual", "convert", "batched", "mlp"]
+
+
+def gb_kernel_launches():
+    return lib().gb_kernel_launches()
+
+
+def gb_profile_enable(on):
+    return lib().gb_profile_enable(int(bool(on)))
+
+
+def gb_profile_read(kind):
+    n, ms, fl, by = i64(), dbl(), dbl(), dbl()
+    st = lib().gb_profile_read(kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by))
+    if st != 0:
+        raise GbError("gb_profile_read", st)
+    return dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
+
+
+# ---- torch-tensor conveniences ---------------------------------------------------
+
+def _colmajor(t, name):
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if t.numel() > 0 and t.stride(0) != 1 and t.shape[0] > 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    return t.data_ptr(), max(1, t.stride(1) if t.shape[1] > 1 else t.shape[0])
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def trsm(side, uplo, trans, diag, alpha, A, B, plan=None, stream=None):
+    """Solve in place on torch CUDA tensors (float64 or float32, column-major).
+
+    B (m x n) is overwritten by X.  Raises GbError on a nonzero status.
+    """
+    import torch
+    m, n = B.shape
+    pa, lda = _colmajor(A, "A")
+    pb, ldb = _colmajor(B, "B")
+    s = _stream_handle(stream)
+    if B.dtype == torch.float64:
+        st = gb_dtrsm_plan(side, uplo, trans, diag, m, n, float(alpha), pa, lda, pb, ldb, plan, s)
+        fn = "gb_dtrsm_plan"
+    elif B.dtype == torch.float32:
+        st = gb_strsm_plan(side, uplo, trans, diag, m, n, float(alpha), pa, lda, pb, ldb, plan, s)
+        fn = "gb_strsm_plan"
+    else:
+        raise TypeError(f"unsupported dtype {B.dtype}")
+    if st != 0:
+        raise GbError(fn, st)
+    return B
+
+
+def colmajor_empty(m, n, dtype, device="cuda"):
+    """An m x n column-major torch tensor (a transposed row-major buffer)."""
+    import torch
+    return torch.empty((n, m), dtype=dtype, device=device).t()
+
+
+def to_device_colmajor(x, dtype=None, device="cuda"):
+    """Copy a numpy/torch 2-D array to a column-major CUDA tensor."""
+    import numpy as np
+    import torch
+    t = torch.as_tensor(np.asarray(x)) if not isinstance(x, torch.Tensor) else x
+    if dtype is not None:
+        t = t.to(dtype)
+    out = colmajor_empty(t.shape[0], t.shape[1], t.dtype, device)
+    out.copy_(t)
+    return out

@@ -1,0 +1,247 @@
+// Diagonal-block triangular solve: the paper's TS task (Section IV, stages 1
+// and 3; the white triangles of Figs. 2-4), for one nr x nr block with
+// nr <= 64 and all right-hand sides of the canonical view.
+//
+// Design (GB300): one thread owns one right-hand side; its nb entries live in
+// registers for the whole solve (fully unrolled substitution), the triangle
+// sits in shared memory and is read with broadcast vector loads, and the B
+// panel is staged through shared memory so that global loads and stores are
+// coalesced whichever way B is laid out.  The diagonal is inverted once per
+// CTA, so each step is a multiply (FP64: DFMA-bound; the whole block costs
+// nr^2/2 multiply-adds per right-hand side).
+#include "common.cuh"
+
+namespace gb {
+namespace {
+
+constexpr int kDiagCols = 64;  // right-hand sides per CTA (one per thread)
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct Vec<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+
+// Shared-memory layout (dynamic):
+//   L  [NB][NB]   column form (MT=false): L[k*NB + i] = Mv(i,k)
+//                 row form    (MT=true) : L[i*NB + k] = Mv(i,k)
+//   inv[NB]       1 / Mv(i,i)  (1 for a unit diagonal or padding rows)
+//   Bs [NB][kDiagCols + 1]
+template <typename T, int NB>
+constexpr size_t diag_smem_bytes()
+{
+    return sizeof(T) * (size_t(NB) * NB + NB + size_t(NB) * (kDiagCols + 1));
+}
+
+// FWD: Mv lower (forward substitution); MT: Mv(i,j) = A(j,i); LEFT: Bv
+// column-major.  Msub = &A(r0, r0), Bsub = &Bv(r0, 0).
+template <typename T, int NB, bool FWD, bool MT, bool LEFT>
+__global__ void __launch_bounds__(kDiagCols)
+diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
+                  int64_t ldb, int nr, int64_t ncols, T alpha, int unit)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *L = reinterpret_cast<T *>(smem_raw);
+    T *inv = L + NB * NB;
+    T *Bs = inv + NB;
+    constexpr int BS = kDiagCols + 1;
+
+    const int tid = threadIdx.x;
+    const int64_t c0 = int64_t(blockIdx.x) * kDiagCols;
+    const int ncb = (int)((ncols - c0) < kDiagCols ? (ncols - c0) : kDiagCols);
+
+    // ---- triangle -> shared memory (only the referenced strict triangle) --
+    // Global A is column-major; Mv(i,k) = MT ? A(k,i) : A(i,k).  The loop
+    // index runs fastest over A's contiguous dimension.
+    for (int idx = tid; idx < NB * NB; idx += kDiagCols) {
+        int fast = idx % NB, slow = idx / NB;  // fast = row of A, slow = col of A
+        int i = MT ? slow : fast;              // row of Mv
+        int k = MT ? fast : slow;              // col of Mv
+        bool ref = (i < nr) && (k < nr) && (FWD ? (k < i) : (k > i));
+        T v = ref ? Msub[fast + int64_t(slow) * lda] : T(0);
+        // column form stores Mv(:,k) contiguously, row form Mv(i,:)
+        L[MT ? (i * NB + k) : (k * NB + i)] = v;
+    }
+    for (int i = tid; i < NB; i += kDiagCols) {
+        T d = T(1);
+        if (i < nr && !unit) d = T(1) / Msub[i + int64_t(i) * lda];
+        inv[i] = d;
+    }
+    // ---- B panel -> shared memory, coalesced ------------------------------
+    if (LEFT) {  // Bv(i,c) = Bsub[i + c*ldb]: contiguous in i
+        for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
+            int i = idx % NB, c = idx / NB;
+            T v = T(0);
+            if (i < nr && c < ncb) v = Bsub[i + (c0 + c) * ldb];
+            Bs[i * BS + c] = v;
+        }
+    } else {     // Bv(i,c) = Bsub[c + i*ldb]: contiguous in c
+        for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
+            int c = idx % kDiagCols, i = idx / kDiagCols;
+            T v = T(0);
+            if (i < nr && c < ncb) v = Bsub[(c0 + c) + int64_t(i) * ldb];
+            Bs[i * BS + c] = v;
+        }
+    }
+    __syncthreads();
+
+    // ---- substitution in registers ----------------------------------------
+    T t[NB];
+#pragma unroll
+    for (int i = 0; i < NB; i++) t[i] = alpha * Bs[i * BS + tid];
+
+    using V = typename Vec<T>::type;
+    constexpr int VN = Vec<T>::n;
+    if (!MT) {
+        // column (axpy) form: once x_k is known, subtract Mv(:,k) x_k
+        if (FWD) {
+#pragma unroll
+            for (int k = 0; k < NB; k++) {
+                T x = t[k] * inv[k];
+                t[k] = x;
+#pragma unroll
+                for (int i0 = ((k + 1) / VN) * VN; i0 < NB; i0 += VN) {
+                    V v = *reinterpret_cast<const V *>(&L[k * NB + i0]);
+                    const T *vv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                    for (int e = 0; e < VN; e++)
+                        if (i0 + e > k) t[i0 + e] -= vv[e] * x;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = NB - 1; k >= 0; k--) {
+                T x = t[k] * inv[k];
+                t[k] = x;
+#pragma unroll
+                for (int i0 = 0; i0 < k; i0 += VN) {
+                    V v = *reinterpret_cast<const V *>(&L[k * NB + i0]);
+                    const T *vv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                    for (int e = 0; e < VN; e++)
+                        if (i0 + e < k) t[i0 + e] -= vv[e] * x;
+                }
+            }
+        }
+    } else {
+        // row (dot) form: x_i = (t_i - Mv(i,:) x) / Mv(i,i), two partial sums
+        if (FWD) {
+#pragma unroll
+            for (int i = 0; i < NB; i++) {
+                T s0 = t[i], s1 = T(0);
+#pragma unroll
+                for (int k0 = 0; k0 < i; k0 += VN) {
+                    V v = *reinterpret_cast<const V *>(&L[i * NB + k0]);
+                    const T *vv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                    for (int e = 0; e < VN; e++)
+                        if (k0 + e < i) {
+                            if (((k0 + e) & 1) == 0) s0 -= vv[e] * t[k0 + e];
+                            else s1 -= vv[e] * t[k0 + e];
+                        }
+                }
+                t[i] = (s0 + s1) * inv[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = NB - 1; i >= 0; i--) {
+                T s0 = t[i], s1 = T(0);
+#pragma unroll
+                for (int k0 = ((i + 1) / VN) * VN; k0 < NB; k0 += VN) {
+                    V v = *reinterpret_cast<const V *>(&L[i * NB + k0]);
+                    const T *vv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                    for (int e = 0; e < VN; e++)
+                        if (k0 + e > i) {
+                            if (((k0 + e) & 1) == 0) s0 -= vv[e] * t[k0 + e];
+                            else s1 -= vv[e] * t[k0 + e];
+                        }
+                }
+                t[i] = (s0 + s1) * inv[i];
+            }
+        }
+    }
+
+#pragma unroll
+    for (int i = 0; i < NB; i++) Bs[i * BS + tid] = t[i];
+    __syncthreads();
+
+    // ---- write back, coalesced --------------------------------------------
+    if (LEFT) {
+        for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
+            int i = idx % NB, c = idx / NB;
+            if (i < nr && c < ncb) Bsub[i + (c0 + c) * ldb] = Bs[i * BS + c];
+        }
+    } else {
+        for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
+            int c = idx % kDiagCols, i = idx / kDiagCols;
+            if (i < nr && c < ncb) Bsub[(c0 + c) + int64_t(i) * ldb] = Bs[i * BS + c];
+        }
+    }
+}
+
+template <typename T, int NB, bool FWD, bool MT, bool LEFT>
+int launch_nb(const T *Msub, int64_t lda, T *Bsub, int64_t ldb, int nr, int64_t ncols,
+              T alpha, int unit, cudaStream_t s)
+{
+    auto kern = diag_solve_kernel<T, NB, FWD, MT, LEFT>;
+    constexpr size_t smem = diag_smem_bytes<T, NB>();
+    static bool attr_done = false;  // per instantiation; idempotent if raced
+    if (!attr_done) {
+        GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_done = true;
+    }
+    int64_t grid = (ncols + kDiagCols - 1) / kDiagCols;
+    if (grid > 0x7fffffff) return GB_STATUS_CUDA_ERROR;
+    LaunchScope ls(KK_DIAG, s, double(nr) * nr * ncols,
+                   sizeof(T) * (0.5 * nr * nr + 2.0 * nr * ncols));
+    kern<<<(unsigned)grid, kDiagCols, smem, s>>>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit);
+    return check(cudaGetLastError());
+}
+
+template <typename T, bool FWD, bool MT, bool LEFT>
+int launch_dir(const T *Msub, int64_t lda, T *Bsub, int64_t ldb, int nr, int64_t ncols,
+               T alpha, int unit, cudaStream_t s)
+{
+    if (nr <= 16) return launch_nb<T, 16, FWD, MT, LEFT>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit, s);
+    if (nr <= 32) return launch_nb<T, 32, FWD, MT, LEFT>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit, s);
+    return launch_nb<T, 64, FWD, MT, LEFT>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit, s);
+}
+
+}  // namespace
+
+template <typename T>
+int launch_diag_solve(const Canon<T> &c, int64_t r0, int nr, T alpha)
+{
+    if (nr <= 0 || c.ncols <= 0) return 0;
+    if (nr > 64) return GB_STATUS_CUDA_ERROR;  // driver never asks for more
+    const T *Msub = c.A + r0 + r0 * c.lda;
+    T *Bsub = bv_ptr(c, r0, 0);
+    int unit = c.unit ? 1 : 0;
+#define GB_DIAG_CASE(F, M, L)                                                             \
+    if (c.forward == F && c.mt == M && c.left == L)                                       \
+        return launch_dir<T, F, M, L>(Msub, c.lda, Bsub, c.ldb, nr, c.ncols, alpha, unit, \
+                                      c.stream);
+    GB_DIAG_CASE(true, false, true)
+    GB_DIAG_CASE(true, false, false)
+    GB_DIAG_CASE(true, true, true)
+    GB_DIAG_CASE(true, true, false)
+    GB_DIAG_CASE(false, false, true)
+    GB_DIAG_CASE(false, false, false)
+    GB_DIAG_CASE(false, true, true)
+    GB_DIAG_CASE(false, true, false)
+#undef GB_DIAG_CASE
+    return GB_STATUS_CUDA_ERROR;
+}
+
+template int launch_diag_solve<double>(const Canon<double> &, int64_t, int, double);
+template int launch_diag_solve<float>(const Canon<float> &, int64_t, int, float);
+
+}  // namespace gb

@@ -1,0 +1,109 @@
+"""GPU parity of the plain FP64 / FP32 solve against the CPU oracle.
+
+Acceptance: FP64 normwise relative forward error <= 1e-12 and backward error
+<= 10 k 2^-53; FP32 forward error <= 1e-4 (k = order of the triangle).
+All sixteen side/uplo/trans/diag forms, ragged sizes around the 16/32/64
+block edges, every driver of the paper's three computation models
+(Section V; Section VI states that they give the same results), NaN-poisoned
+unreferenced entries, alpha = 0, padded leading dimensions with canaries.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_19917_gb300 import inputs
+from tests.helpers import U64, bwd_err, fwd_err, gpu_solve
+
+pytestmark = pytest.mark.gpu
+
+COMBOS = list(itertools.product((0, 1), (0, 1), (0, 1), (0, 1)))
+SHAPES = [(1, 1), (2, 3), (7, 31), (31, 7), (32, 33), (33, 32), (63, 64), (64, 65),
+          (65, 1), (1, 65), (255, 256), (256, 255), (257, 257), (300, 17)]
+TOL = {"f64": 1e-12, "f32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2305_19917_gb300 import build
+    build.build()
+
+
+def _check(side, uplo, trans, diag, m, n, alpha, dtype, plan=None, seed=0, ldpad=0, poison=False):
+    A, B = inputs.make_problem(side, uplo, trans, diag, m, n, seed, poison=poison)
+    Xo = oracle.dtrsm(side, uplo, trans, diag, alpha, A, B)
+    X, pad_ok = gpu_solve(side, uplo, trans, diag, alpha, A, B, dtype=dtype, plan=plan, ldpad=ldpad)
+    assert pad_ok, "wrote outside the m x n matrix"
+    assert np.all(np.isfinite(X))
+    fe = fwd_err(X, Xo)
+    assert fe <= TOL[dtype], (side, uplo, trans, diag, m, n, fe)
+    if dtype == "f64" and m * n > 0:
+        k = m if side == 0 else n
+        Aclean = inputs.make_problem(side, uplo, trans, diag, m, n, seed)[0]
+        eta = bwd_err(side, uplo, trans, diag, alpha, Aclean, B, X)
+        assert eta <= 10 * k * U64, (side, uplo, trans, diag, m, n, eta)
+    return fe
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("side,uplo,trans,diag", COMBOS)
+def test_all_forms_ragged_sizes(side, uplo, trans, diag, dtype):
+    for i, (m, n) in enumerate(SHAPES):
+        _check(side, uplo, trans, diag, m, n, 1.5, dtype, seed=i, ldpad=3 if i % 2 else 0)
+
+
+def test_config_one_256x64():
+    """Left/Lower/N/NonUnit, m=256, n=64, alpha=1, seed 0."""
+    fe = _check(0, 0, 0, 0, 256, 64, 1.0, "f64", seed=0)
+    assert fe <= 1e-12
+
+
+DRIVERS = [(0, nb, 0) for nb in (16, 32, 64, 128, 256, 512)] + \
+          [(1, nb, d) for nb in (16, 64, 128) for d in (1, 2, 4, 7)] + \
+          [(2, nb, 0) for nb in (16, 64, 256)]
+
+
+@pytest.mark.parametrize("driver,nb,depth", DRIVERS)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_three_models_agree(driver, nb, depth, dtype):
+    plan = dict(driver=driver, nb=nb, depth=depth)
+    for side, uplo, trans, diag in [(0, 0, 0, 0), (0, 1, 1, 1), (1, 0, 1, 0), (1, 1, 0, 1),
+                                    (0, 1, 0, 0), (1, 0, 0, 1)]:
+        _check(side, uplo, trans, diag, 700, 130, -0.5, dtype, plan=plan, seed=3)
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", COMBOS)
+def test_unreferenced_nan_is_not_read(side, uplo, trans, diag):
+    for dtype in ("f64", "f32"):
+        _check(side, uplo, trans, diag, 200, 90, 1.5, dtype, seed=5, poison=True,
+               plan=dict(driver=1, nb=32, depth=2))
+
+
+def test_alpha_zero_sets_zero_without_reading_a():
+    A = np.full((50, 50), np.nan)
+    B = np.random.default_rng(0).standard_normal((50, 20))
+    for side in (0, 1):
+        k = 50 if side == 0 else 20
+        X, _ = gpu_solve(side, 0, 0, 0, 0.0, A[:k, :k], B)
+        assert np.array_equal(X, np.zeros_like(B))
+
+
+def test_config_scale_sampled_columns():
+    """m = n = 16384 (the benchmark's launch configuration): the GPU solve vs
+    the oracle on sampled right-hand sides (each column of X depends only on
+    its own column of B)."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    m = n = 16384
+    A, B = inputs.make_problem(0, 0, 0, 0, m, n, seed=0)
+    Ad = api.to_device_colmajor(A, torch.float64)
+    Bd = api.to_device_colmajor(B, torch.float64)
+    api.trsm(0, 0, 0, 0, 1.5, Ad, Bd)
+    torch.cuda.synchronize()
+    cols = [0, 1, 4097, 8191, 12000, n - 1]
+    X = Bd[:, cols].cpu().numpy()
+    Xo = oracle.dtrsm(0, 0, 0, 0, 1.5, A, B[:, cols])
+    assert fwd_err(X, Xo) <= 1e-12
+    eta = bwd_err(0, 0, 0, 0, 1.5, A, B[:, cols], X)
+    assert eta <= 10 * m * U64
