@@ -144,6 +144,37 @@ int gb_profile_enable(int on);
 int gb_profile_read(int kind, int64_t *launches, double *ms, double *flops,
                     double *bytes);
 
+/*
+ * gb_bf16_gemm_update: the tensor-core gemm task of the mixed-precision
+ * path (Section IV stage 2, b.low -= L.mid x.up, with many right-hand
+ * sides), exposed for testing and reuse:
+ *     C = alpha * C - A * B
+ *   1 M, 2 N, 3 K       sizes; K must be a multiple of 64 (K == 0: no-op)
+ *   4 A   device BF16, M x K row-major (element (i,k) at A[i*lda + k]),
+ *         16-byte aligned
+ *   5 lda >= max(K, 8), multiple of 8
+ *   6 B   device BF16, K x N column-major (element (k,j) at B[k + j*ldb]),
+ *         16-byte aligned
+ *   7 ldb >= max(K, 8), multiple of 8
+ *   8 C   device FP32, M x N column-major
+ *   9 ldc >= max(1, M)
+ *  10 alpha, 11 stream
+ * Products are exact, sums accumulate in FP32 (tcgen05, tensor memory).
+ * Asynchronous.  A device-side wait that times out is reported by
+ * gb_device_status().
+ */
+int gb_bf16_gemm_update(int64_t M, int64_t N, int64_t K, const void *A,
+                        int64_t lda, const void *B, int64_t ldb, float *C,
+                        int64_t ldc, float alpha, void *stream);
+
+/*
+ * gb_device_status: synchronises with the current device and returns the
+ * library's device-side status word (0 = no error, GB_STATUS_TIMEOUT-class
+ * codes 1..3 = a bounded wait of a tensor-core kernel expired); clears it
+ * when `clear` is nonzero.  Returns GB_STATUS_CUDA_ERROR if it cannot read.
+ */
+int gb_device_status(int clear);
+
 /* Message for a status code (static storage). */
 const char *gb_status_string(int status);
 /* Last CUDA error code seen by the library on this host thread (0 = none). */

@@ -48,6 +48,8 @@ _SIGS = {
     "gb_status_string": ([i32], ctypes.c_char_p),
     "gb_last_cuda_error": ([], i32),
     "gb_version": ([], i32),
+    "gb_bf16_gemm_update": ([i64, i64, i64, vp, i64, vp, i64, vp, i64, flt, vp], i32),
+    "gb_device_status": ([i32], i32),
     "gb_kernel_launches": ([], ctypes.c_uint64),
     "gb_profile_enable": ([i32], i32),
     "gb_profile_read": ([i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
@@ -108,6 +110,14 @@ def gb_plan_counts(plan, k):
         raise GbError("gb_plan_counts", st)
     return dict(n_diag=nd.value, n_gemm=ng.value, n_offdiag_blocks=nbk.value,
                 gemm_madds_per_col=md.value)
+
+
+def gb_bf16_gemm_update(M, N, K, A, lda, B, ldb, C, ldc, alpha, stream=0):
+    return lib().gb_bf16_gemm_update(M, N, K, A, lda, B, ldb, C, ldc, alpha, stream or None)
+
+
+def gb_device_status(clear=1):
+    return lib().gb_device_status(clear)
 
 
 def gb_status_string(status):

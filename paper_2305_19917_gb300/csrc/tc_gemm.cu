@@ -1,0 +1,253 @@
+// Tensor-core GEMM update C = alpha*C - A*B on sm_103a (tcgen05 + TMA): the
+// paper's gemm task (Section IV stage 2, Section V) in the low-precision
+// solve of the mixed-precision path.  A (M x K) and B (K x N) are BF16, the
+// product accumulates in FP32 in tensor memory, C is FP32.
+//
+// Layout: A row-major (K-major), B column-major (K-major as the MMA's B
+// operand), C column-major.  One CTA per 128 x 256 output tile; K advances in
+// 64-element steps (one 128-byte swizzle row) through a 4-stage TMA ring.
+// Warp roles: warp 0 issues TMA loads, warp 1 owns TMEM and issues the MMAs
+// (one elected thread), warps 2-5 drain the accumulator (each warp reads the
+// 32 TMEM lanes its rank allows) and apply the FP32 epilogue with coalesced
+// column-major stores.
+#include <cstdio>
+#include "common.cuh"
+#include "tc_common.cuh"
+
+namespace gb {
+
+// ---- host: tensor-map encoding through the driver entry point ---------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+int encode_tmap(CUtensorMap *map, CUtensorMapDataType dt, int rank, const void *base, const uint64_t *dims,
+                const uint64_t *strides_bytes, const uint32_t *box)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return GB_STATUS_CUDA_ERROR;
+    cuuint64_t gd[5], gs[4];
+    cuuint32_t bx[5], es[5];
+    for (int i = 0; i < rank; i++) {
+        gd[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (i + 1 < rank) gs[i] = strides_bytes[i];
+    }
+    CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void *>(base), gd, gs, bx, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_cuda_error(cudaErrorInvalidValue);
+        return GB_STATUS_CUDA_ERROR;
+    }
+    return 0;
+}
+
+// ---- device status word (timeouts of bounded waits) -------------------------
+static int *g_status[64] = {nullptr};
+
+int *device_status_word()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!g_status[dev]) {
+        int *p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+        g_status[dev] = p;
+    }
+    return g_status[dev];
+}
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr size_t SMEM_BYTES = 1024 + STAGES * size_t(STAGE_BYTES) + 256;
+
+__global__ void __launch_bounds__(192, 1)
+tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    float *__restrict__ C, int64_t ldc, int M, int N, int K, float alpha, int *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + STAGES * A_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accf + 1);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m_blk = blockIdx.y, n_blk = blockIdx.x;
+    const int nk = K / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(accf, 1);
+        abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, BN);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    volatile int *ab = &abort_flag;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::tma_prefetch_desc(&tmA);
+            tc::tma_prefetch_desc(&tmB);
+            for (int kt = 0; kt < nk; kt++) {
+                const int s = kt % STAGES;
+                const uint32_t ph = (kt / STAGES) & 1;
+                if (!tc::mbar_wait(&empty[s], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) break;
+                tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                tc::tma_load_2d(&tmA, &full[s], sA + s * A_BYTES, kt * BK, m_blk * BM);
+                tc::tma_load_2d(&tmB, &full[s], sB + s * B_BYTES, kt * BK, n_blk * BN);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            for (int kt = 0; kt < nk; kt++) {
+                const int s = kt % STAGES;
+                const uint32_t ph = (kt / STAGES) & 1;
+                if (!tc::mbar_wait(&full[s], ph, ab, status, tc::TC_TIMEOUT_MMA)) break;
+                tc::tc_fence_after();
+                const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
+                const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; kk++) {
+                    tc::mma_f16(tmem, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
+                                idesc, (kt | kk) != 0);
+                }
+                tc::mma_commit(&empty[s]);
+            }
+            tc::mma_commit(accf);
+        }
+    } else {
+        // epilogue: 4 warps, warp w reads TMEM lanes 32*(w%4) .. +31
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const int64_t gi = int64_t(m_blk) * BM + row;
+        if (tc::mbar_wait(accf, 0, ab, status, tc::TC_TIMEOUT_EPILOGUE)) {
+            tc::tc_fence_after();
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c0), r);
+                tc::tmem_ld_wait();
+                if (gi < M) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int64_t gj = int64_t(n_blk) * BN + c0 + j;
+                        if (gj < N) {
+                            float *p = C + gi + gj * ldc;
+                            *p = alpha * *p - __uint_as_float(r[j]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, BN);
+    }
+}
+
+}  // namespace
+
+// C (M x N, FP32, column-major, ldc) = alpha*C - A*B with A (M x K, BF16
+// row-major, lda) and B (K x N, BF16 column-major, ldb).  K % 64 == 0,
+// lda % 8 == 0, ldb % 8 == 0, A and B 16-byte aligned.
+int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
+                        int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return 0;
+    if (K <= 0 || K % BK || lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) ||
+        (reinterpret_cast<uintptr_t>(B) & 15))
+        return GB_STATUS_CUDA_ERROR;
+    if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
+    CUtensorMap ta, tb;
+    {
+        uint64_t dims[2] = {uint64_t(K), uint64_t(M)};
+        uint64_t strides[1] = {uint64_t(lda) * 2};
+        uint32_t box[2] = {BK, BM};
+        GB_TRY(encode_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, strides, box));
+    }
+    {
+        uint64_t dims[2] = {uint64_t(K), uint64_t(N)};
+        uint64_t strides[1] = {uint64_t(ldb) * 2};
+        uint32_t box[2] = {BK, BN};
+        GB_TRY(encode_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, strides, box));
+    }
+    static bool attr = false;
+    if (!attr) {
+        GB_CUDA(cudaFuncSetAttribute(tc_gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_BYTES));
+        attr = true;
+    }
+    int *st = device_status_word();
+    if (!st) return GB_STATUS_CUDA_ERROR;
+    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+    if (grid.y > 65535) return GB_STATUS_CUDA_ERROR;
+    LaunchScope ls(KK_GEMM_TC, s, 2.0 * M * N * K, 2.0 * (double(M) * K + double(K) * N) + 8.0 * M * N);
+    tc_gemm_bf16_kernel<<<grid, 192, SMEM_BYTES, s>>>(ta, tb, C, ldc, (int)M, (int)N, (int)K, alpha, st);
+    return check(cudaGetLastError());
+}
+
+}  // namespace gb
+
+extern "C" int gb_bf16_gemm_update(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
+                                   int64_t ldb, float *C, int64_t ldc, float alpha, void *stream)
+{
+    if (M < 0) return -1;
+    if (N < 0) return -2;
+    if (K < 0 || K % 64) return -3;
+    if (A == nullptr && M * N * K > 0) return -4;
+    if (lda < (K > 8 ? K : 8) || lda % 8) return -5;
+    if (B == nullptr && M * N * K > 0) return -6;
+    if (ldb < (K > 8 ? K : 8) || ldb % 8) return -7;
+    if (C == nullptr && M * N > 0) return -8;
+    if (ldc < (M > 1 ? M : 1)) return -9;
+    if (M == 0 || N == 0) return 0;
+    if (K == 0) return 0;
+    return gb::launch_tc_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, alpha, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int gb_device_status(int clear)
+{
+    int *p = gb::device_status_word();
+    if (!p) return GB_STATUS_CUDA_ERROR;
+    int v = 0;
+    if (cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GB_STATUS_CUDA_ERROR;
+    if (clear && v) cudaMemset(p, 0, sizeof(int));
+    return v;
+}
