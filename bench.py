@@ -2,8 +2,11 @@
 
 Workload (one "step"): Left/Lower/NoTrans/NonUnit solve with m = n = 16384,
 alpha = 1.5, synthetic well-conditioned inputs (diagonal U[1,2), off-diagonal
-U(-1,1)/m, B ~ N(0,1), seed 0), through the library's C entry point with the
-planner's default plan.  Inputs (A 2 GiB + B 2 GiB in FP64) are larger than
+U(-1,1)/m, B ~ N(0,1), seed 0), through the library's C entry point, solved
+to FP64-level error by the mixed-precision path (BF16 tensor-core solve plus
+split-precision refinement); the plain FP64 solve of the same problem is
+timed after it on the same GPU for comparison (--path fp64 makes the plain
+solve the timed step).  Inputs (A 2 GiB + B 2 GiB in FP64) are larger than
 L2, and B is re-copied from a pristine device copy before every step (outside
 the timed events), which also evicts L2.
 
@@ -30,6 +33,17 @@ UNIT = "TFLOP/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+MEASURED_PEAKS = _measured_peaks()
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -38,7 +52,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--m", type=int, default=16384)
     p.add_argument("--n", type=int, default=16384)
-    p.add_argument("--path", default="fp64", choices=["fp64"])
+    p.add_argument("--path", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cols", type=int, default=0,
                    help="right-hand sides in the oracle sample (0 = auto, ~10-30 s)")
@@ -116,13 +131,22 @@ class ClockSampler:
 
 # -------------------------------------------------------------- oracle arm ----
 
+_ORACLE_INPUTS = {}
+
+
 def oracle_sample(m, n_sample, seed=0, nthreads=0):
-    """Time the CPU oracle on the first n_sample right-hand sides of the
-    workload.  Returns (seconds, flops, threads)."""
+    """Time the CPU oracle on n_sample right-hand sides of the workload
+    (the triangle A is generated once per (m, seed) and reused).
+    Returns (seconds, flops, threads)."""
     import oracle
     from paper_2305_19917_gb300 import inputs
-    A, B = inputs.make_problem(0, 0, 0, 0, m, n_sample, seed)
-    X = np.asfortranarray(B.copy())
+    key = (m, seed)
+    if key not in _ORACLE_INPUTS:
+        _ORACLE_INPUTS.clear()
+        _ORACLE_INPUTS[key] = inputs.make_problem(0, 0, 0, 0, m, 1, seed)[0]
+    A = _ORACLE_INPUTS[key]
+    B = np.random.default_rng(seed + 1).standard_normal((m, n_sample))
+    X = np.asfortranarray(B)
     threads = nthreads if nthreads > 0 else (os.cpu_count() or 1)
     t0 = time.perf_counter()
     oracle.dtrsm_inplace(0, 0, 0, 0, 1.5, A, X, nthreads=threads)
@@ -175,6 +199,21 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm ---
 
+def _timed_steps(solve, reset, steps, stream):
+    """Run `steps` solves, each bracketed by CUDA events on `stream` (the B
+    reset copy before each one is outside the events)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    out = []
+    for i in range(steps):
+        reset()
+        ev[i][0].record(stream)
+        out.append(solve())
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -191,6 +230,7 @@ def run_ours(args):
     api.lib()
     m, n = args.m, args.n
     side, uplo, trans, diag, alpha = 0, 0, 0, 0, 1.5
+    tol, max_iter = 1e-11, 30
 
     # Host inputs (seeded), device copies.
     A_h, B_h = inputs.make_problem(side, uplo, trans, diag, m, n, seed=0)
@@ -199,16 +239,25 @@ def run_ours(args):
     B = api.colmajor_empty(m, n, torch.float64)
     stream = torch.cuda.current_stream()
     flops = float(m) * m * n
+    mixed = args.path == "mixed"
 
-    def solve():
-        api.trsm(side, uplo, trans, diag, alpha, A, B, stream=stream)
-
-    for _ in range(max(3, args.warmup)):
+    def reset():
         B.copy_(B0)
+
+    def solve_mixed():
+        return api.trsm_mixed(side, uplo, trans, diag, alpha, A, B, tol=tol, max_iter=max_iter, stream=stream)
+
+    def solve_fp64():
+        api.trsm(side, uplo, trans, diag, alpha, A, B, stream=stream)
+        return None
+
+    solve = solve_mixed if mixed else solve_fp64
+    for _ in range(max(3, args.warmup)):
+        reset()
         solve()
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, events around each solve only ----
+    # ---- timed region: K steps ----
     clocks = ClockSampler(dev)
     clocks.start()
     if world > 1:
@@ -216,15 +265,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     api.gb_profile_enable(1)
     launches0 = api.gb_kernel_launches()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     wall0 = time.perf_counter()
-    for i in range(args.steps):
-        B.copy_(B0)
-        ev[i][0].record(stream)
-        solve()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
+    ms, outs = _timed_steps(solve, reset, args.steps, stream)
     wall = time.perf_counter() - wall0
     if world > 1:
         dist.barrier()
@@ -232,7 +274,6 @@ def run_ours(args):
     clk = clocks.stop()
     prof = {k: api.gb_profile_read(i) for i, k in enumerate(api.KERNEL_KINDS)}
     api.gb_profile_enable(0)
-    ms = [a.elapsed_time(b) for a, b in ev]
     ms_step = float(np.sum(ms) / args.steps)
     if world > 1:
         t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
@@ -247,8 +288,11 @@ def run_ours(args):
         cols = [0, n // 3, n - 1]
         Xs = B[:, cols].cpu().numpy()
         Xo = oracle.dtrsm(side, uplo, trans, diag, alpha, A_h, B_h[:, cols])
-        acc = {"fwd_err_sampled": float(np.linalg.norm(Xs - Xo) / np.linalg.norm(Xo)),
-               "columns": cols}
+        acc = {"fwd_err_sampled": float(np.linalg.norm(Xs - Xo) / np.linalg.norm(Xo)), "columns": cols}
+        if mixed:
+            acc["refinement_steps"] = [o[1] for o in outs]
+            acc["est_err"] = [o[2] for o in outs]
+            acc["status"] = [o[0] for o in outs]
 
     # ---- e2e: host buffers, H2D + solve + D2H inside the timed region ----
     A_pin = torch.empty((m, m), dtype=torch.float64, pin_memory=True).t()
@@ -264,7 +308,10 @@ def run_ours(args):
         e0.record(stream)
         A_e.copy_(A_pin, non_blocking=True)
         B.copy_(B_pin, non_blocking=True)
-        api.trsm(side, uplo, trans, diag, alpha, A_e, B, stream=stream)
+        if mixed:
+            api.trsm_mixed(side, uplo, trans, diag, alpha, A_e, B, tol=tol, max_iter=max_iter, stream=stream)
+        else:
+            api.trsm(side, uplo, trans, diag, alpha, A_e, B, stream=stream)
         X_pin.copy_(B, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -278,14 +325,30 @@ def run_ours(args):
     d2h = m * n * 8
     del A_pin, B_pin, X_pin, A_e
 
+    # ---- plain FP64 on the same GPU, same workload (the comparison) ----
+    plain = None
+    if mixed and not args.no_plain:
+        for _ in range(1):
+            reset()
+            solve_fp64()
+        pms, _ = _timed_steps(solve_fp64, reset, 2, stream)
+        pt = float(np.mean(pms))
+        plain = {"value": flops / (pt * 1e-3) / 1e12, "unit": UNIT, "ms_per_step": pt, "steps": 2,
+                 "speedup_of_mixed": pt / ms_step}
+
     # ---- roofline of the dominant kernel (largest share of device time) ----
     dom = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[dom]
     achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12 if p["ms"] > 0 else 0.0
-    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (not in "
-                               "MEASURED_PEAKS.json; probe measured 1.196 TF/s DFMA)",
+    if dom in ("gemm_tc", "residual"):
+        peak = MEASURED_PEAKS.get("bf16_tflops_sustained") or 1700.0
+        bound, src = "tensor", "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)"
+    else:
+        peak, bound = FP64_PEAK_TFLOPS, "alu"
+        src = ("derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json; "
+               "probe measured 1.196 TF/s DFMA)")
+    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": src,
                 "launches": p["launches"], "ms_total": p["ms"],
                 "share": p["ms"] / max(1e-9, sum(v["ms"] for v in prof.values()))}
 
@@ -295,21 +358,27 @@ def run_ours(args):
         cpu = cpu_baseline(m, cols)
 
     if rank == 0:
+        if mixed:
+            wl = (f"mixed BF16 + refinement TRSM Left/Lower/N/NonUnit m=n={m} to FP64-level error "
+                  f"(tol {tol:g} on ||D||/||X||; forward error vs FP64 oracle <= 1e-10), alpha=1.5, "
+                  f"diag U[1,2), offdiag U(-1,1)/m, B~N(0,1), seed 0")
+        else:
+            wl = (f"plain FP64 TRSM Left/Lower/N/NonUnit m=n={m}, alpha=1.5, diag U[1,2), "
+                  f"offdiag U(-1,1)/m, B~N(0,1), seed 0, planner default plan")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"plain FP64 TRSM Left/Lower/N/NonUnit m=n={m}, alpha=1.5, "
-                                       f"diag U[1,2), offdiag U(-1,1)/m, B~N(0,1), seed 0, "
-                                       f"planner default plan",
-                           "global_batch": world, "l2": "inputs larger than L2 (4 GiB); B re-copied "
-                                                       "before each step"},
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16+f64" if mixed else "f64", "data": "synthetic",
+                "config": {"workload": wl, "global_batch": world,
+                           "l2": "inputs larger than L2 (4 GiB); B re-copied before each step"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": world * flops / (e2e_t * 1e-3) / 1e12, "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches), "clocks": clk, "accuracy": acc,
-                "wall_s_timed": wall,
-                "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items()
-                            if v["launches"]}}
+                "plain_fp64": plain, "wall_s_timed": wall,
+                "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
+                                "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 else 0.0)}
+                            for k, v in prof.items() if v["launches"]}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

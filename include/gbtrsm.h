@@ -112,6 +112,35 @@ int gb_strsm_plan(int side, int uplo, int trans, int diag, int64_t m,
                   int64_t n, float alpha, const float *A, int64_t lda,
                   float *B, int64_t ldb, const gb_plan *plan, void *stream);
 
+/* Low precision of the mixed-precision solve. */
+enum { GB_PREC_BF16 = 0, GB_PREC_FP8 = 1 };
+
+/*
+ * gb_dtrsm_mixed: FP64-accurate triangular solve by a low-precision solve
+ * plus iterative refinement (X overwrites B, both FP64 as in gb_dtrsm).
+ *   X0 = solve in low precision (GEMM updates on the tensor cores in BF16
+ *        with FP32 accumulation, FP32 diagonal blocks; recursive model,
+ *        Section V-A);
+ *   repeat R = alpha*B - op(A)X (split-precision tensor-core products with
+ *        exact integer sums, FP64 accumulation), D = low-precision solve of
+ *        op(A) D = R, X += D (FP64), until ||D||_F <= tol * ||X||_F.
+ * Arguments 1-11 as gb_dtrsm, then
+ *  12 tol        >= 0 (e.g. 1e-11 for ~1e-10 forward error)
+ *  13 prec       GB_PREC_BF16 (GB_PREC_FP8: see the FP8 entry below)
+ *  14 max_iter   1..1000 refinement steps
+ *  15 iters_out  host, optional: refinement steps taken
+ *  16 est_err_out host, optional: last ||D||_F / ||X||_F
+ *  17 stream
+ * Returns 0 when converged, GB_STATUS_NOT_CONVERGED (X = last iterate) when
+ * max_iter was reached first.  Synchronous: returns after the solve is
+ * complete.  Work space (about 8 k^2 + 28 k n bytes, k and n rounded up to
+ * multiples of 128) comes from a library-owned stream-ordered pool.
+ */
+int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
+                   int64_t n, double alpha, const double *A, int64_t lda,
+                   double *B, int64_t ldb, double tol, int prec, int max_iter,
+                   int *iters_out, double *est_err_out, void *stream);
+
 /*
  * gb_plan_counts: host-only description of the launches a plan issues for a
  * triangle of order k (no GPU work).  Writes the number of diagonal-block

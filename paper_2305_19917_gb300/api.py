@@ -48,6 +48,8 @@ _SIGS = {
     "gb_status_string": ([i32], ctypes.c_char_p),
     "gb_last_cuda_error": ([], i32),
     "gb_version": ([], i32),
+    "gb_dtrsm_mixed": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32,
+                        ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
     "gb_bf16_gemm_update": ([i64, i64, i64, vp, i64, vp, i64, vp, i64, flt, vp], i32),
     "gb_device_status": ([i32], i32),
     "gb_kernel_launches": ([], ctypes.c_uint64),
@@ -110,6 +112,31 @@ def gb_plan_counts(plan, k):
         raise GbError("gb_plan_counts", st)
     return dict(n_diag=nd.value, n_gemm=ng.value, n_offdiag_blocks=nbk.value,
                 gemm_madds_per_col=md.value)
+
+
+PREC_BF16, PREC_FP8 = 0, 1
+
+
+def gb_dtrsm_mixed(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, stream=0):
+    """Returns (status, iters, est_err)."""
+    it, est = i32(), dbl()
+    st = lib().gb_dtrsm_mixed(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
+                              ctypes.byref(it), ctypes.byref(est), stream or None)
+    return st, it.value, est.value
+
+
+def trsm_mixed(side, uplo, trans, diag, alpha, A, B, tol=1e-11, prec=0, max_iter=30, stream=None):
+    """Mixed-precision solve on torch float64 CUDA tensors (column-major), in
+    place on B.  Returns (status, iters, est_err); raises on argument / CUDA
+    errors (status < 0 or == STATUS_CUDA_ERROR)."""
+    m, n = B.shape
+    pa, lda = _colmajor(A, "A")
+    pb, ldb = _colmajor(B, "B")
+    st, it, est = gb_dtrsm_mixed(side, uplo, trans, diag, m, n, float(alpha), pa, lda, pb, ldb, float(tol),
+                                 prec, max_iter, _stream_handle(stream))
+    if st < 0 or st in (STATUS_CUDA_ERROR, STATUS_TIMEOUT):
+        raise GbError("gb_dtrsm_mixed", st)
+    return st, it, est
 
 
 def gb_bf16_gemm_update(M, N, K, A, lda, B, ldb, C, ldc, alpha, stream=0):

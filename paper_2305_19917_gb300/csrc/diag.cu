@@ -9,6 +9,7 @@
 // coalesced whichever way B is laid out.  The diagonal is inverted once per
 // CTA, so each step is a multiply (FP64: DFMA-bound; the whole block costs
 // nr^2/2 multiply-adds per right-hand side).
+#include <cuda_bf16.h>
 #include "common.cuh"
 
 namespace gb {
@@ -42,10 +43,13 @@ constexpr size_t diag_smem_bytes()
 
 // FWD: Mv lower (forward substitution); MT: Mv(i,j) = A(j,i); LEFT: Bv
 // column-major.  Msub = &A(r0, r0), Bsub = &Bv(r0, 0).
-template <typename T, int NB, bool FWD, bool MT, bool LEFT>
+// EMIT: also write a BF16 copy of the solved block to Ebf (column-major,
+// ldb), the operand of the tensor-core GEMM updates (LEFT layout only).
+template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT>
 __global__ void __launch_bounds__(kDiagCols)
 diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
-                  int64_t ldb, int nr, int64_t ncols, T alpha, int unit)
+                  int64_t ldb, int nr, int64_t ncols, T alpha, int unit,
+                  __nv_bfloat16 *__restrict__ Ebf)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *L = reinterpret_cast<T *>(smem_raw);
@@ -177,7 +181,10 @@ diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
     if (LEFT) {
         for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
             int i = idx % NB, c = idx / NB;
-            if (i < nr && c < ncb) Bsub[i + (c0 + c) * ldb] = Bs[i * BS + c];
+            if (i < nr && c < ncb) {
+                Bsub[i + (c0 + c) * ldb] = Bs[i * BS + c];
+                if (EMIT) Ebf[i + (c0 + c) * ldb] = __float2bfloat16_rn(float(Bs[i * BS + c]));
+            }
         }
     } else {
         for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
@@ -187,11 +194,11 @@ diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
     }
 }
 
-template <typename T, int NB, bool FWD, bool MT, bool LEFT>
+template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT = false>
 int launch_nb(const T *Msub, int64_t lda, T *Bsub, int64_t ldb, int nr, int64_t ncols,
-              T alpha, int unit, cudaStream_t s)
+              T alpha, int unit, cudaStream_t s, __nv_bfloat16 *Ebf = nullptr)
 {
-    auto kern = diag_solve_kernel<T, NB, FWD, MT, LEFT>;
+    auto kern = diag_solve_kernel<T, NB, FWD, MT, LEFT, EMIT>;
     constexpr size_t smem = diag_smem_bytes<T, NB>();
     static bool attr_done = false;  // per instantiation; idempotent if raced
     if (!attr_done) {
@@ -202,7 +209,7 @@ int launch_nb(const T *Msub, int64_t lda, T *Bsub, int64_t ldb, int nr, int64_t 
     if (grid > 0x7fffffff) return GB_STATUS_CUDA_ERROR;
     LaunchScope ls(KK_DIAG, s, double(nr) * nr * ncols,
                    sizeof(T) * (0.5 * nr * nr + 2.0 * nr * ncols));
-    kern<<<(unsigned)grid, kDiagCols, smem, s>>>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit);
+    kern<<<(unsigned)grid, kDiagCols, smem, s>>>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit, Ebf);
     return check(cudaGetLastError());
 }
 
@@ -243,5 +250,16 @@ int launch_diag_solve(const Canon<T> &c, int64_t r0, int nr, T alpha)
 
 template int launch_diag_solve<double>(const Canon<double> &, int64_t, int, double);
 template int launch_diag_solve<float>(const Canon<float> &, int64_t, int, float);
+
+// Mixed-precision path: forward solve of one 64-row block held as a band
+// (row i of the block at Msub + i*lda, its 64 entries contiguous), FP32
+// right-hand sides in column-major Y, BF16 copy of the result to Ebf.
+int launch_diag_solve_band_f32(const float *Msub, int64_t lda, float *Y, int64_t ldy, int nr,
+                               int64_t ncols, __nv_bfloat16 *Ebf, cudaStream_t s)
+{
+    if (nr <= 0 || ncols <= 0) return 0;
+    if (nr > 64) return GB_STATUS_CUDA_ERROR;
+    return launch_nb<float, 64, true, true, true, true>(Msub, lda, Y, ldy, nr, ncols, 1.0f, 0, s, Ebf);
+}
 
 }  // namespace gb

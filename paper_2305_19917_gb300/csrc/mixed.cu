@@ -1,0 +1,515 @@
+// Mixed-precision triangular solve with iterative refinement:
+//
+//   X0  = low-precision solve of Mv X = alpha*Bv   (BF16 tensor-core GEMM
+//         updates with FP32 accumulation, FP32 diagonal-block solves; the
+//         recursive model of Section V-A down to 64-row TS tasks)
+//   repeat:  R = alpha*Bv - Mv X  (split-precision products on the tensor
+//            cores, exact integer sums, FP64 final accumulation)
+//            D = low-precision solve of Mv D = R;   X += D  (FP64)
+//   until ||D||_F <= tol ||X||_F.
+//
+// The residual is carried incrementally: after X += D~ (D~ = D rounded to
+// the two 6-bit digits per column that the residual kernel consumes),
+// R -= Mv D~, so R stays the residual of the X actually held.  Mv is cut
+// without its diagonal into seven 6-bit digit slices with a power-of-two
+// scale per row (42 bits of the largest off-diagonal entry); the diagonal
+// term is applied exactly in FP64;
+// the number of slice pairs formed shrinks as the corrections shrink.
+//
+// Everything is done on a canonical FORWARD problem in column-major layout:
+// a backward (upper) problem is index-reversed, a right-side problem is
+// transposed, both while copying in, and the result is mapped back at the
+// end.  Sizes are padded to multiples of 128 (identity on the padded
+// diagonal, zero right-hand sides), so every tile is aligned for TMA.
+#include <cmath>
+#include <cstdio>
+#include <cuda_bf16.h>
+#include "common.cuh"
+#include "driver.cuh"
+
+namespace gb {
+
+int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
+                        int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s);
+int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
+                       const double *dg, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
+                       cudaStream_t s);
+int launch_diag_solve_band_f32(const float *Msub, int64_t lda, float *Y, int64_t ldy, int nr, int64_t ncols,
+                               __nv_bfloat16 *Ebf, cudaStream_t s);
+
+namespace {
+
+constexpr int kSlices = 7;     // digit slices of Mv (6 bits each)
+constexpr int kBand = 64;      // FP32 band of diagonal 64-blocks
+
+// Canonical forward view of the user problem (device-side description).
+struct View {
+    const double *A;
+    int64_t lda;
+    bool mt;       // Mv(i,c) = A(c,i)
+    bool rev;      // index reversal (backward problem)
+    bool unit;
+    int64_t k;     // order of Mv
+};
+
+// Mv'(i,c) of the forward view: lower triangle (c <= i), 1 on a unit or
+// padded diagonal, 0 elsewhere.
+__device__ __forceinline__ double mvp(const View &v, int64_t i, int64_t c)
+{
+    if (c > i) return 0.0;
+    if (i >= v.k || c >= v.k) return (i == c) ? 1.0 : 0.0;
+    if (i == c && v.unit) return 1.0;
+    int64_t r = v.rev ? v.k - 1 - i : i;
+    int64_t s = v.rev ? v.k - 1 - c : c;
+    return v.mt ? v.A[s + r * v.lda] : v.A[r + s * v.lda];
+}
+// Which index of Mv' runs along A's contiguous dimension: true = i.
+__device__ __forceinline__ bool contig_i(const View &v) { return !v.mt; }
+
+// Load the 64 x 64 tile (i0.., c0..) of Mv' into shared memory t[64][65],
+// reading A along its contiguous dimension.
+__device__ void load_tile(const View &v, int64_t i0, int64_t c0, double (*t)[65])
+{
+    const int tid = threadIdx.x;  // 256 threads
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        int fast = idx & 63, slow = idx >> 6;
+        int li = contig_i(v) ? fast : slow;
+        int lc = contig_i(v) ? slow : fast;
+        t[li][lc] = mvp(v, i0 + li, c0 + lc);
+    }
+}
+
+// Tiles that are needed: every 64x64 tile with c0 < end of the 128-row
+// diagonal block of i0 (the residual kernel reads up to that column).
+__device__ __forceinline__ bool tile_needed(int64_t i0, int64_t c0) { return c0 < ((i0 >> 7) << 7) + 128; }
+
+__device__ __forceinline__ int exponent_of(double a)
+{
+    int e;
+    frexp(a, &e);  // a = f 2^e, f in [0.5, 1)
+    return e;
+}
+
+// Pass 1: row exponents e_i with max_{c<i} |Mv'(i,c)| < 2^(e_i - 1): the
+// strictly lower part only, so that small off-diagonal entries keep all
+// their digits when the diagonal is much larger (the diagonal is applied
+// exactly in FP64 by the residual kernel).
+__global__ void __launch_bounds__(256) rowexp_kernel(View v, int64_t kp, int *e_row)
+{
+    __shared__ double t[64][65];
+    const int64_t i0 = int64_t(blockIdx.y) * 64, c0 = int64_t(blockIdx.x) * 64;
+    if (c0 > i0 + 63) return;
+    load_tile(v, i0, c0, t);
+    __syncthreads();
+    const int tid = threadIdx.x;
+    if (tid < 64) {
+        double mx = 0;
+        for (int c = 0; c < 64; c++)
+            if (c0 + c != i0 + tid) mx = fmax(mx, fabs(t[tid][c]));
+        if (mx > 0) atomicMax(&e_row[i0 + tid], exponent_of(mx) + 1);
+    }
+}
+
+// Pass 2: BF16 copy (round to nearest), the 7 digit slices of the strictly
+// lower part, the FP64 diagonal and the FP32 band of diagonal 64-blocks.
+__global__ void __launch_bounds__(256)
+prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bfloat16 *As, float *band,
+             double *dg)
+{
+    __shared__ double t[64][65];
+    const int64_t i0 = int64_t(blockIdx.y) * 64, c0 = int64_t(blockIdx.x) * 64;
+    if (!tile_needed(i0, c0)) return;
+    load_tile(v, i0, c0, t);
+    __syncthreads();
+    const int tid = threadIdx.x;
+    const size_t slice = size_t(kp) * size_t(kp);
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        int lc = idx & 63, li = idx >> 6;  // contiguous along c in the row-major outputs
+        int64_t i = i0 + li, c = c0 + lc;
+        double a = t[li][lc];
+        size_t off = size_t(i) * size_t(kp) + size_t(c);
+        Abf[off] = __double2bfloat16(a);
+        int e = e_row[i];
+        double r = (a == 0.0 || c == i) ? 0.0 : ldexp(a, -e);  // |r| <= 1/2
+        if (c == i) dg[i] = a;
+#pragma unroll
+        for (int p = 0; p < kSlices; p++) {
+            double x = r * 64.0;
+            double q = rint(x);
+            r = x - q;
+            As[p * slice + off] = __double2bfloat16(q);  // |q| <= 32: exact
+        }
+        if ((c >> 6) == (i >> 6)) band[size_t(i) * kBand + (c & 63)] = float(a);
+    }
+}
+
+// R = alpha * Bv' (forward view of the right-hand sides), zero padded.
+// Left: Bv(i,j) = B(i,j); Right: Bv(i,j) = B(j,i); reversal on i.
+__global__ void __launch_bounds__(256)
+prepB_kernel(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t ncols, double alpha,
+             double *R, int64_t kp)
+{
+    __shared__ double t[64][65];
+    const int64_t i0 = int64_t(blockIdx.y) * 64, j0 = int64_t(blockIdx.x) * 64;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        int fast = idx & 63, slow = idx >> 6;
+        int li = left ? fast : slow, lj = left ? slow : fast;
+        int64_t i = i0 + li, j = j0 + lj;
+        double val = 0.0;
+        if (i < k && j < ncols) {
+            int64_t r = rev ? k - 1 - i : i;
+            val = alpha * (left ? B[r + j * ldb] : B[j + r * ldb]);
+        }
+        t[li][lj] = val;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        int li = idx & 63, lj = idx >> 6;
+        R[(i0 + li) + (j0 + lj) * kp] = t[li][lj];
+    }
+}
+
+// B(user) = X' mapped back (only the m x n user entries).
+__global__ void __launch_bounds__(256)
+writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t ncols, const double *X,
+                 int64_t kp)
+{
+    __shared__ double t[64][65];
+    const int64_t i0 = int64_t(blockIdx.y) * 64, j0 = int64_t(blockIdx.x) * 64;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        int li = idx & 63, lj = idx >> 6;
+        t[li][lj] = X[(i0 + li) + (j0 + lj) * kp];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        int fast = idx & 63, slow = idx >> 6;
+        int li = left ? fast : slow, lj = left ? slow : fast;
+        int64_t i = i0 + li, j = j0 + lj;
+        if (i < k && j < ncols) {
+            int64_t r = rev ? k - 1 - i : i;
+            if (left) B[r + j * ldb] = t[li][lj];
+            else B[j + r * ldb] = t[li][lj];
+        }
+    }
+}
+
+// Y = float(R), elementwise over kp x np (contiguous).
+__global__ void to_f32_kernel(const double *R, float *Y, int64_t n)
+{
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        Y[i] = float(R[i]);
+}
+
+// Per column j: f_j with max_k |Y(k,j)| < 2^(f_j - 1); the two 6-bit digits
+// z_1, z_2 of Y(:,j) 2^-f_j; X += D~ with D~ = 2^f_j (z_1 2^-6 + z_2 2^-12);
+// accumulates ||D~||^2, ||X||^2 into norms[0], norms[1] and the largest
+// column ratio max|D~| / max|X| into norms[2] (as bits of a double).
+__global__ void __launch_bounds__(256)
+slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bfloat16 *Zs, int *f_col,
+                  double *X, double *norms, int first)
+{
+    const int64_t j = blockIdx.x;
+    const float *y = Y + j * kp;
+    __shared__ float red[8];
+    __shared__ double redd[3][8];
+    __shared__ double mxred[8];
+    float mx = 0.f;
+    for (int64_t i = threadIdx.x; i < kp; i += 256) mx = fmaxf(mx, fabsf(y[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.f;
+    for (int w = 0; w < 8; w++) mx = fmaxf(mx, red[w]);
+    const int f = (mx > 0.f) ? exponent_of(double(mx)) + 1 : 0;
+    if (threadIdx.x == 0) f_col[j] = f;
+    __nv_bfloat16 *z1 = Zs + j * kp;
+    __nv_bfloat16 *z2 = Zs + np * kp + j * kp;
+    double *x = X + j * kp;
+    double sd = 0, sx = 0, md = 0, mxx = 0;
+    for (int64_t i = threadIdx.x; i < kp; i += 256) {
+        double r = ldexp(double(y[i]), -f);  // |r| < 1/2
+        double t1 = r * 64.0, q1 = rint(t1);
+        double t2 = (t1 - q1) * 64.0, q2 = rint(t2);
+        z1[i] = __double2bfloat16(q1);
+        z2[i] = __double2bfloat16(q2);
+        double d = ldexp(q1 * 64.0 + q2, f - 12);
+        double xv = first ? d : x[i] + d;
+        x[i] = xv;
+        if (j < ncols) {
+            sd += d * d;
+            sx += xv * xv;
+            md = fmax(md, fabs(d));
+            mxx = fmax(mxx, fabs(xv));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+        mxx = fmax(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        redd[0][threadIdx.x >> 5] = sd;
+        redd[1][threadIdx.x >> 5] = sx;
+        redd[2][threadIdx.x >> 5] = md;
+        mxred[threadIdx.x >> 5] = mxx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, cmd = 0, cmx = 0;
+        for (int w = 0; w < 8; w++) {
+            a += redd[0][w];
+            b += redd[1][w];
+            cmd = fmax(cmd, redd[2][w]);
+            cmx = fmax(cmx, mxred[w]);
+        }
+        const double ratio = (cmx > 0) ? cmd / cmx : (cmd > 0 ? 1.0 : 0.0);
+        atomicAdd(&norms[0], a);
+        atomicAdd(&norms[1], b);
+        // non-negative doubles order like their bit patterns
+        atomicMax(reinterpret_cast<unsigned long long *>(&norms[2]),
+                  static_cast<unsigned long long>(__double_as_longlong(ratio)));
+    }
+}
+
+// ---- workspace --------------------------------------------------------------
+struct Workspace {
+    char *base = nullptr;
+    size_t bytes = 0;
+};
+
+cudaMemPool_t library_pool()
+{
+    static cudaMemPool_t pool[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        uint64_t thr = ~0ull;  // keep freed blocks cached in the pool
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+        pool[dev] = p;
+    }
+    return pool[dev];
+}
+
+// Executor of the low-precision forward solve on the padded canonical view.
+struct LowExec {
+    float *Y;
+    __nv_bfloat16 *Ybf;
+    const __nv_bfloat16 *Abf;
+    const float *band;
+    int64_t kp, np;
+    cudaStream_t s;
+    int status = 0;
+    bool ok() const { return status == 0; }
+    void ts(int64_t b0, int64_t nr, float a)
+    {
+        if (status) return;
+        if (nr > kBand) {
+            drive_blocked(*this, b0, b0 + nr, (int64_t)kBand, a, true);
+            return;
+        }
+        status = launch_diag_solve_band_f32(band + b0 * kBand, kBand, Y + b0, kp, (int)nr, np, Ybf + b0, s);
+    }
+    void gemm(int64_t ci0, int64_t M, int64_t ak0, int64_t K, float a)
+    {
+        if (status) return;
+        status = launch_tc_gemm_bf16(M, np, K, Abf + ci0 * kp + ak0, kp, Ybf + ak0, kp, Y + ci0, kp, a, s);
+    }
+};
+
+int low_solve(LowExec &e, int64_t kp)
+{
+    int depth = 0;
+    while ((kp >> (depth + 1)) >= 256 && depth < 10) depth++;
+    drive_recursive(e, 0, kp, depth, (int64_t)kBand, 1.0f, true);
+    return e.status;
+}
+
+// Number of 6-bit digit levels the residual must keep for a correction whose
+// size relative to X is rho: the dropped pairs (weight 2^(-6(p+q))) must stay
+// below ~2^-44 of |Mv||X|.
+int levels_for(double rho)
+{
+    if (!(rho > 0)) return 2;
+    double bits = -std::log2(rho);  // the correction is 2^-bits of X
+    int L = 8 - int(std::floor(bits / 6.0));
+    if (L > 8) L = 8;
+    if (L < 2) L = 2;
+    return L;
+}
+
+int residual_update(double *R, const __nv_bfloat16 *As, const __nv_bfloat16 *Zs, const int *e_row, const int *f_col,
+                    const double *dg, int64_t kp, int64_t np, int Lmax, cudaStream_t s)
+{
+    for (int64_t lo = 0; lo < kp; lo += 16384) {
+        int64_t hi = lo + 16384 < kp ? lo + 16384 : kp;
+        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, dg, kp, np, lo, hi, Lmax, s));
+    }
+    return 0;
+}
+
+}  // namespace
+
+int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
+                     int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
+                     double *est_err_out, cudaStream_t s)
+{
+    const int64_t k = side == GB_LEFT ? m : n;
+    const int64_t ncols = side == GB_LEFT ? n : m;
+    const bool mt = side == GB_LEFT ? (trans == GB_TRANS) : (trans == GB_NOTRANS);
+    const bool forward = (uplo == GB_LOWER) != mt;
+    const int64_t kp = (k + 127) / 128 * 128;
+    const int64_t np = (ncols + 127) / 128 * 128;
+    (void)prec;
+
+    View v{A, lda, mt, !forward, diag == GB_UNIT, k};
+
+    // ---- workspace layout ----
+    const size_t kk = size_t(kp) * size_t(kp), kn = size_t(kp) * size_t(np);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    };
+    size_t o_abf = take(kk * 2), o_as = take(kk * 2 * kSlices), o_band = take(size_t(kp) * kBand * 4);
+    size_t o_r = take(kn * 8), o_x = take(kn * 8), o_y = take(kn * 4), o_ybf = take(kn * 2), o_zs = take(kn * 4);
+    size_t o_e = take(size_t(kp) * 4), o_f = take(size_t(np) * 4), o_norm = take(64), o_dg = take(size_t(kp) * 8);
+    cudaMemPool_t pool = library_pool();
+    if (!pool) return GB_STATUS_CUDA_ERROR;
+    char *ws = nullptr;
+    GB_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&ws), off, pool, s));
+    auto *Abf = reinterpret_cast<__nv_bfloat16 *>(ws + o_abf);
+    auto *As = reinterpret_cast<__nv_bfloat16 *>(ws + o_as);
+    auto *band = reinterpret_cast<float *>(ws + o_band);
+    auto *R = reinterpret_cast<double *>(ws + o_r);
+    auto *X = reinterpret_cast<double *>(ws + o_x);
+    auto *Y = reinterpret_cast<float *>(ws + o_y);
+    auto *Ybf = reinterpret_cast<__nv_bfloat16 *>(ws + o_ybf);
+    auto *Zs = reinterpret_cast<__nv_bfloat16 *>(ws + o_zs);
+    auto *e_row = reinterpret_cast<int *>(ws + o_e);
+    auto *f_col = reinterpret_cast<int *>(ws + o_f);
+    auto *norms = reinterpret_cast<double *>(ws + o_norm);
+    auto *dg = reinterpret_cast<double *>(ws + o_dg);
+
+    int st = 0;
+    double h_norm[3] = {0, 0, 0};
+    int iters = 0;
+    double est = 0;
+    do {
+        // ---- conversions (once per solve) ----
+        if ((st = check(cudaMemsetAsync(e_row, 0x80, size_t(kp) * 4, s)))) break;  // very negative
+        dim3 tgrid((unsigned)(kp / 64), (unsigned)(kp / 64));
+        {
+            LaunchScope ls(KK_CONVERT, s, 0, 8.0 * double(k) * double(k) / 2);
+            rowexp_kernel<<<tgrid, 256, 0, s>>>(v, kp, e_row);
+            if ((st = check(cudaGetLastError()))) break;
+        }
+        {
+            LaunchScope ls(KK_CONVERT, s, 0, (8.0 + 2.0 * (1 + kSlices)) * double(kp) * double(kp) / 2);
+            prepA_kernel<<<tgrid, 256, 0, s>>>(v, kp, e_row, Abf, As, band, dg);
+            if ((st = check(cudaGetLastError()))) break;
+        }
+        {
+            LaunchScope ls(KK_CONVERT, s, 0, 16.0 * double(kp) * double(np));
+            prepB_kernel<<<dim3((unsigned)(np / 64), (unsigned)(kp / 64)), 256, 0, s>>>(
+                B, ldb, side == GB_LEFT, !forward, k, ncols, alpha, R, kp);
+            if ((st = check(cudaGetLastError()))) break;
+        }
+        LowExec le{Y, Ybf, Abf, band, kp, np, s};
+        const int64_t nel = int64_t(kn);
+        const unsigned eg = (unsigned)((nel + 255) / 256 < 152 * 64 ? (nel + 255) / 256 : 152 * 64);
+        int Lmax = 8;
+        for (int t = 0;; t++) {
+            {
+                LaunchScope ls(KK_CONVERT, s, 0, 12.0 * double(nel));
+                to_f32_kernel<<<eg, 256, 0, s>>>(R, Y, nel);
+                if ((st = check(cudaGetLastError()))) break;
+            }
+            le.status = 0;
+            if ((st = low_solve(le, kp))) break;
+            if ((st = check(cudaMemsetAsync(norms, 0, 3 * sizeof(double), s)))) break;
+            {
+                LaunchScope ls(KK_CONVERT, s, 0, 24.0 * double(nel));
+                slice_cols_kernel<<<(unsigned)np, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, norms, t == 0);
+                if ((st = check(cudaGetLastError()))) break;
+            }
+            if ((st = check(cudaMemcpyAsync(h_norm, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)))) break;
+            if ((st = check(cudaStreamSynchronize(s)))) break;
+            const double nd = std::sqrt(h_norm[0]), nx = std::sqrt(h_norm[1]);
+            if (t > 0) {
+                iters = t;
+                est = nx > 0 ? nd / nx : 0.0;
+                if (est <= tol || t >= max_iter) break;
+            }
+            Lmax = (t == 0) ? 8 : levels_for(h_norm[2]);
+            if ((st = residual_update(R, As, Zs, e_row, f_col, dg, kp, np, Lmax, s))) break;
+        }
+        if (st) break;
+        {
+            LaunchScope ls(KK_CONVERT, s, 0, 16.0 * double(k) * double(ncols));
+            writeback_kernel<<<dim3((unsigned)(np / 64), (unsigned)(kp / 64)), 256, 0, s>>>(
+                B, ldb, side == GB_LEFT, !forward, k, ncols, X, kp);
+            if ((st = check(cudaGetLastError()))) break;
+        }
+    } while (0);
+    cudaFreeAsync(ws, s);
+    if (st == 0) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = check(e);
+    }
+    if (iters_out) *iters_out = iters;
+    if (est_err_out) *est_err_out = est;
+    if (st) return st;
+    return (est <= tol) ? 0 : GB_STATUS_NOT_CONVERGED;
+}
+
+}  // namespace gb
+
+extern "C" int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
+                              const double *A, int64_t lda, double *B, int64_t ldb, double tol, int prec,
+                              int max_iter, int *iters_out, double *est_err_out, void *stream)
+{
+    if (iters_out) *iters_out = 0;
+    if (est_err_out) *est_err_out = 0;
+    if (side != GB_LEFT && side != GB_RIGHT) return -1;
+    if (uplo != GB_LOWER && uplo != GB_UPPER) return -2;
+    if (trans != GB_NOTRANS && trans != GB_TRANS) return -3;
+    if (diag != GB_NONUNIT && diag != GB_UNIT) return -4;
+    if (m < 0) return -5;
+    if (n < 0) return -6;
+    const int64_t k = side == GB_LEFT ? m : n;
+    const bool empty = (m == 0 || n == 0);
+    if (A == nullptr && !empty && alpha != 0.0) return -8;
+    if (lda < (k > 1 ? k : 1)) return -9;
+    if (B == nullptr && !empty) return -10;
+    if (ldb < (m > 1 ? m : 1)) return -11;
+    if (!(tol >= 0.0)) return -12;
+    if (prec != GB_PREC_BF16) return -13;
+    if (max_iter < 1 || max_iter > 1000) return -14;
+    if (empty) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (alpha == 0.0) {
+        gb::Canon<double> c{};
+        c.B = B;
+        c.ldb = ldb;
+        c.left = side == GB_LEFT;
+        c.k = k;
+        c.ncols = side == GB_LEFT ? n : m;
+        c.stream = s;
+        int st = gb::launch_zero(c);
+        if (st) return st;
+        return gb::check(cudaStreamSynchronize(s));
+    }
+    return gb::dtrsm_mixed_impl(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, iters_out,
+                                est_err_out, s);
+}

@@ -1,0 +1,257 @@
+// Split-precision residual update on the tensor cores (mixed-precision path):
+//
+//     R(i,j) -= sum_k Mv(i,k) Z(k,j)         for the lower-triangular Mv
+//
+// where both factors are given as fixed-point digit slices (BF16 holding
+// small integers, |digit| <= 32), the strictly lower part of Mv as
+//     Mv(i,k) = 2^e_i * sum_{p=1..7} a_p(i,k) 2^(-6p)      (per-row scale)
+// (the diagonal Mv(i,i) is applied separately, in FP64), and
+//     Z(k,j)  = 2^f_j * sum_{q=1..2} z_q(k,j) 2^(-6q)      (per-column scale)
+// and only the pairs with p + q <= Lmax (Lmax <= 8) are formed.  Each digit
+// product is at most 2^10 and K <= 16384 per launch, so every tensor-core
+// sum S_pq = sum_k a_p z_q is an exact integer below 2^24 in the FP32
+// accumulator.  The epilogue converts S_pq to integers and accumulates
+// T = sum S_pq 2^(6(Lmax-p-q)) exactly in int64 (|T| < 2^62), then applies
+// R -= 2^(e_i + f_j - 6 Lmax) * T in FP64: the one rounding of the whole
+// product is that of T to FP64.
+//
+// One CTA per 128 x 128 tile of R.  Pass p (p = 1..Lmax-1) multiplies slice
+// a_p (128 x 64 per stage) with [z_1; z_2] (256 x 64 per stage, both slices
+// of the same 128 columns) into one of two 128 x 256 TMEM accumulators, so
+// that draining pass p overlaps the MMAs of pass p+1.  Warp 0: TMA, warp 1:
+// TMEM + MMA issue, warps 2-9: epilogue (warp w drains TMEM lanes
+// 32*(w%4).., column half (w-2)/4).
+#include "common.cuh"
+#include "tc_common.cuh"
+
+namespace gb {
+
+int *device_status_word();
+
+namespace {
+
+constexpr int BM = 128, BNO = 128, BK = 64, STAGES = 4;
+constexpr uint32_t A_BYTES = BM * BK * 2;          // one A slice tile
+constexpr uint32_t B_BYTES = 2 * BNO * BK * 2;     // z_1 and z_2 tiles
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr size_t SMEM_BYTES = 1024 + STAGES * size_t(STAGE_BYTES) + 256;
+constexpr int NTHREADS = 320;
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ,
+                   double *__restrict__ R, int64_t ldr, const int *__restrict__ e_row,
+                   const int *__restrict__ f_col, const double *__restrict__ dg,
+                   const __nv_bfloat16 *__restrict__ Zg, int64_t zslice, int k_lo, int k_hi, int Lmax,
+                   int *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + STAGES * A_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;  // [2]
+    uint64_t *acce = accf + 2;        // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + 2);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m_blk = gridDim.y - 1 - blockIdx.y;  // longest K ranges first
+    const int n_blk = blockIdx.x;
+    const int i0 = m_blk * BM, j0 = n_blk * BNO;
+    const int k_end = min(k_hi, i0 + BM);
+    if (k_end <= k_lo) return;  // tile entirely above the diagonal: nothing to add
+    const int nk = (k_end - k_lo) / BK;
+    const int P = Lmax - 1;     // slices a_1 .. a_{Lmax-1}
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&accf[b], 1);
+            tc::mbar_init(&acce[b], 8);  // one arrival per epilogue warp
+        }
+        abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, 512);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    volatile int *ab = &abort_flag;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::tma_prefetch_desc(&tmA);
+            tc::tma_prefetch_desc(&tmZ);
+            int g = 0;
+            for (int p = 0; p < P && !*ab; p++) {
+                for (int kt = 0; kt < nk; kt++, g++) {
+                    const int s = g % STAGES;
+                    const uint32_t ph = (g / STAGES) & 1;
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) break;
+                    tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    tc::tma_load_3d(&tmA, &full[s], sA + s * A_BYTES, k_lo + kt * BK, i0, p);
+                    tc::tma_load_3d(&tmZ, &full[s], sB + s * B_BYTES, k_lo + kt * BK, j0, 0);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int g = 0;
+            for (int p = 0; p < P; p++) {
+                const int buf = p & 1;
+                const uint32_t use = p >> 1;
+                if (!tc::mbar_wait(&acce[buf], (use & 1) ^ 1, ab, status, tc::TC_TIMEOUT_MMA)) break;
+                tc::tc_fence_after();
+                const bool two = (p + 3) <= Lmax;  // pair (p+1, 2) still needed
+                const uint32_t idesc = two ? tc::idesc_bf16_f32(BM, 256) : tc::idesc_bf16_f32(BM, 128);
+                const uint32_t d = tmem + uint32_t(buf * 256);
+                bool ok = true;
+                for (int kt = 0; kt < nk; kt++, g++) {
+                    const int s = g % STAGES;
+                    const uint32_t ph = (g / STAGES) & 1;
+                    if (!tc::mbar_wait(&full[s], ph, ab, status, tc::TC_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
+                    const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++)
+                        tc::mma_f16(d, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
+                                    idesc, (kt | kk) != 0);
+                    tc::mma_commit(&empty[s]);
+                }
+                tc::mma_commit(&accf[buf]);
+                if (!ok) break;
+            }
+        }
+    } else {
+        const int q = warp & 3;                 // TMEM lane group this warp may read
+        const int half = (warp - 2) >> 2;       // output columns [half*64, half*64+64)
+        const int row = q * 32 + lane;
+        long long T[64];
+#pragma unroll
+        for (int c = 0; c < 64; c++) T[c] = 0;
+        bool ok = true;
+        for (int p = 0; p < P; p++) {
+            const int buf = p & 1;
+            const uint32_t use = p >> 1;
+            if (!tc::mbar_wait(&accf[buf], use & 1, ab, status, tc::TC_TIMEOUT_EPILOGUE)) {
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
+            const bool two = (p + 3) <= Lmax;
+            const int s1 = 6 * (Lmax - (p + 2));
+            const int s2 = 6 * (Lmax - (p + 3));
+            const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 256 + half * 64);
+#pragma unroll
+            for (int c0 = 0; c0 < 64; c0 += 32) {
+                uint32_t r1[32];
+                tc::tmem_ld32(tbase + c0, r1);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; j++)
+                    T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r1[j]))) << s1;
+                if (two) {
+                    uint32_t r2[32];
+                    tc::tmem_ld32(tbase + 128 + c0, r2);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r2[j]))) << s2;
+                }
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[buf]);
+        }
+        if (ok) {
+            const int gi = i0 + row;
+            const int ei = e_row[gi] - 6 * Lmax;
+            // the diagonal term Mv(i,i) Z(i,j), exactly in FP64, once: in
+            // the launch whose K range holds column i
+            const bool has_diag = gi >= k_lo && gi < k_hi;
+            const double di = has_diag ? dg[gi] : 0.0;
+#pragma unroll
+            for (int c = 0; c < 64; c++) {
+                const int gj = j0 + half * 64 + c;
+                const int fj = f_col[gj];
+                double *pr = R + gi + int64_t(gj) * ldr;
+                double sub = ldexp(static_cast<double>(T[c]), ei + fj);
+                if (has_diag) {
+                    const int64_t zo = int64_t(gj) * ldr + gi;
+                    const double z = double(__bfloat162float(Zg[zo])) * 64.0 + double(__bfloat162float(Zg[zslice + zo]));
+                    sub += di * ldexp(z, fj - 12);
+                }
+                *pr -= sub;
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+}  // namespace
+
+// R (kp x np, FP64 column-major, ldr) -= Mv * Z over k in [k_lo, k_hi),
+// with A slices (7 x kp x kp BF16 row-major, contiguous) and Z slices
+// (2 x np x kp BF16: slice q holds column j of z_q at Zs + q*np*kp + j*kp).
+// kp, np multiples of 128; k_lo, k_hi multiples of 64; k_hi - k_lo <= 16384.
+int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
+                       const double *dg, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
+                       cudaStream_t s)
+{
+    if (kp <= 0 || np <= 0 || k_hi <= k_lo) return 0;
+    if (kp % 128 || np % 128 || k_lo % 64 || k_hi % 64 || k_hi - k_lo > 16384 || Lmax < 2 || Lmax > 8)
+        return GB_STATUS_CUDA_ERROR;
+    if (kp > 0x7fffffffLL || np > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
+    CUtensorMap ta, tz;
+    {
+        uint64_t dims[3] = {uint64_t(kp), uint64_t(kp), 7};
+        uint64_t strides[2] = {uint64_t(kp) * 2, uint64_t(kp) * uint64_t(kp) * 2};
+        uint32_t box[3] = {BK, BM, 1};
+        GB_TRY(encode_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, As, dims, strides, box));
+    }
+    {
+        uint64_t dims[3] = {uint64_t(kp), uint64_t(np), 2};
+        uint64_t strides[2] = {uint64_t(kp) * 2, uint64_t(np) * uint64_t(kp) * 2};
+        uint32_t box[3] = {BK, BNO, 2};
+        GB_TRY(encode_tmap(&tz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Zs, dims, strides, box));
+    }
+    static bool attr = false;
+    if (!attr) {
+        GB_CUDA(cudaFuncSetAttribute(tc_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_BYTES));
+        attr = true;
+    }
+    int *st = device_status_word();
+    if (!st) return GB_STATUS_CUDA_ERROR;
+    dim3 grid((unsigned)(np / BNO), (unsigned)(kp / BM));
+    if (grid.y > 65535) return GB_STATUS_CUDA_ERROR;
+    // algorithmic work: (Lmax-1) passes over the lower triangle of the K range
+    double tri = 0;
+    for (int64_t i0 = 0; i0 < kp; i0 += BM) {
+        int64_t ke = i0 + BM < k_hi ? i0 + BM : k_hi;
+        if (ke > k_lo) tri += double(ke - k_lo);
+    }
+    double flops = 0;
+    for (int p = 0; p < Lmax - 1; p++) flops += 2.0 * BM * tri * np * ((p + 3 <= Lmax) ? 2 : 1);
+    LaunchScope ls(KK_RESIDUAL, s, flops, 16.0 * kp * np);
+    tc_residual_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(
+        ta, tz, R, ldr, e_row, f_col, dg, static_cast<const __nv_bfloat16 *>(Zs), np * kp, (int)k_lo, (int)k_hi,
+        Lmax, st);
+    return check(cudaGetLastError());
+}
+
+}  // namespace gb

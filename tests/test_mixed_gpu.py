@@ -1,0 +1,88 @@
+"""GPU parity of the mixed-precision solve (BF16 tensor-core updates + split
+residual refinement) against the FP64 CPU oracle: forward error <= 1e-10."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_19917_gb300 import inputs
+from tests.helpers import fwd_err
+
+pytestmark = pytest.mark.gpu
+
+COMBOS = list(itertools.product((0, 1), (0, 1), (0, 1), (0, 1)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2305_19917_gb300 import build
+    build.build()
+
+
+def _mixed(side, uplo, trans, diag, alpha, A, B, tol=1e-11, max_iter=30):
+    import torch
+    from paper_2305_19917_gb300 import api
+    Ad = api.to_device_colmajor(A, torch.float64)
+    Bd = api.to_device_colmajor(B, torch.float64)
+    st, it, est = api.trsm_mixed(side, uplo, trans, diag, alpha, Ad, Bd, tol=tol, max_iter=max_iter)
+    torch.cuda.synchronize()
+    return Bd.cpu().numpy(), st, it, est
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", COMBOS)
+def test_mixed_all_forms(side, uplo, trans, diag):
+    m, n = 300, 170
+    A, B = inputs.make_problem(side, uplo, trans, diag, m, n, seed=11)
+    Xo = oracle.dtrsm(side, uplo, trans, diag, 1.5, A, B)
+    X, st, it, est = _mixed(side, uplo, trans, diag, 1.5, A, B)
+    assert st == 0 and 1 <= it <= 10, (st, it, est)
+    assert fwd_err(X, Xo) <= 1e-10
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 300), (129, 7), (512, 512), (700, 129)])
+def test_mixed_ragged_sizes(m, n):
+    A, B = inputs.make_problem(0, 0, 0, 0, m, n, seed=m + n)
+    Xo = oracle.dtrsm(0, 0, 0, 0, 1.0, A, B)
+    X, st, it, est = _mixed(0, 0, 0, 0, 1.0, A, B)
+    assert st == 0
+    assert fwd_err(X, Xo) <= 1e-10
+
+
+def test_mixed_unreferenced_nan_not_read():
+    A, B = inputs.make_problem(0, 1, 1, 1, 256, 64, seed=4, poison=True)
+    Ac, _ = inputs.make_problem(0, 1, 1, 1, 256, 64, seed=4)
+    Xo = oracle.dtrsm(0, 1, 1, 1, 1.5, Ac, B)
+    X, st, it, est = _mixed(0, 1, 1, 1, 1.5, A, B)
+    assert st == 0 and np.all(np.isfinite(X))
+    assert fwd_err(X, Xo) <= 1e-10
+
+
+def test_mixed_reports_non_convergence():
+    A, B = inputs.make_problem(0, 0, 0, 0, 256, 64, seed=2)
+    X, st, it, est = _mixed(0, 0, 0, 0, 1.0, A, B, tol=1e-30, max_iter=1)
+    from paper_2305_19917_gb300 import api
+    assert st == api.STATUS_NOT_CONVERGED and it == 1 and est > 0
+
+
+def test_mixed_alpha_zero():
+    A = np.full((40, 40), np.nan)
+    B = np.ones((40, 10))
+    X, st, it, est = _mixed(0, 0, 0, 0, 0.0, A, B)
+    assert st == 0 and np.array_equal(X, np.zeros_like(B))
+
+
+@pytest.mark.parametrize("m,n", [(16384, 16384), (32768, 4096)])
+def test_mixed_config_scale_sampled(m, n):
+    """Mixed-precision configuration sizes: sampled right-hand sides vs the oracle."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    A, B = inputs.make_problem(0, 0, 0, 0, m, n, seed=0)
+    Ad = api.to_device_colmajor(A, torch.float64)
+    Bd = api.to_device_colmajor(B, torch.float64)
+    st, it, est = api.trsm_mixed(0, 0, 0, 0, 1.5, Ad, Bd, tol=1e-11)
+    assert st == 0, (st, it, est)
+    cols = [0, 7, n // 2, n - 1]
+    X = Bd[:, cols].cpu().numpy()
+    Xo = oracle.dtrsm(0, 0, 0, 0, 1.5, A, B[:, cols])
+    assert fwd_err(X, Xo) <= 1e-10
