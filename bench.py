@@ -337,7 +337,8 @@ def run_ours(args):
                  "speedup_of_mixed": pt / ms_step}
 
     # ---- roofline of the dominant kernel (largest share of device time) ----
-    dom = max(prof, key=lambda k: prof[k]["ms"])
+    # (a "graph" record is a whole captured sequence of kernels, not one kernel)
+    dom = max((k for k in prof if k != "graph"), key=lambda k: prof[k]["ms"])
     p = prof[dom]
     achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12 if p["ms"] > 0 else 0.0
     if dom in ("gemm_tc", "residual"):

@@ -162,7 +162,7 @@ def gb_version():
     return lib().gb_version()
 
 
-KERNEL_KINDS = ["diag", "gemm_simt", "gemm_tc", "residual", "convert", "batched", "mlp"]
+KERNEL_KINDS = ["diag", "gemm_simt", "gemm_tc", "residual", "convert", "batched", "mlp", "graph"]
 
 
 def gb_kernel_launches():

@@ -73,18 +73,23 @@ enum KernelKind {
     KK_CONVERT = 4,   // precision conversion / slicing / elementwise
     KK_BATCHED = 5,   // persistent batched solve
     KK_MLP = 6,       // cost-model network
-    KK_COUNT = 7
+    KK_GRAPH = 7,     // a CUDA-graph launch (e.g. a captured low-precision solve)
+    KK_COUNT = 8
 };
 // Every kernel launch of the library is wrapped in a LaunchScope: it counts
 // the launch and, while profiling is enabled, brackets it with CUDA events on
 // the launching stream and records its algorithmic flops and bytes.
+// Launches issued while `s` is being captured into a CUDA graph are counted
+// into a per-thread capture counter instead (capture_count()), and the
+// graph launch later adds that many kernels (nkernels).
 struct LaunchScope {
     int kind;
     int slot;
     cudaStream_t stream;
-    LaunchScope(int kind, cudaStream_t s, double flops, double bytes);
+    LaunchScope(int kind, cudaStream_t s, double flops, double bytes, uint64_t nkernels = 1);
     ~LaunchScope();
 };
+uint64_t &capture_count();
 
 // ---- kernel launchers (defined in the .cu files) -------------------------
 

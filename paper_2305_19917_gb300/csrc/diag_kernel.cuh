@@ -1,4 +1,4 @@
-// Diagonal-block triangular solve: the paper's TS task (Section IV, stages 1
+// (internal header) Diagonal-block triangular solve: the paper's TS task (Section IV, stages 1
 // and 3; the white triangles of Figs. 2-4), for one nr x nr block with
 // nr <= 64 and all right-hand sides of the canonical view.
 //
@@ -9,6 +9,7 @@
 // coalesced whichever way B is laid out.  The diagonal is inverted once per
 // CTA, so each step is a multiply (FP64: DFMA-bound; the whole block costs
 // nr^2/2 multiply-adds per right-hand side).
+#pragma once
 #include <cuda_bf16.h>
 #include "common.cuh"
 
@@ -194,16 +195,29 @@ diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
     }
 }
 
+// One-time kernel attribute (dynamic shared memory above 48 KB).
+template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT>
+int diag_prepare()
+{
+    static bool attr_done = false;  // per instantiation; idempotent if raced
+    if (!attr_done) {
+        GB_CUDA(cudaFuncSetAttribute(diag_solve_kernel<T, NB, FWD, MT, LEFT, EMIT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)diag_smem_bytes<T, NB>()));
+        attr_done = true;
+    }
+    return 0;
+}
+
 template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT = false>
 int launch_nb(const T *Msub, int64_t lda, T *Bsub, int64_t ldb, int nr, int64_t ncols,
               T alpha, int unit, cudaStream_t s, __nv_bfloat16 *Ebf = nullptr)
 {
     auto kern = diag_solve_kernel<T, NB, FWD, MT, LEFT, EMIT>;
     constexpr size_t smem = diag_smem_bytes<T, NB>();
-    static bool attr_done = false;  // per instantiation; idempotent if raced
-    if (!attr_done) {
-        GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_done = true;
+    {
+        const int pst = diag_prepare<T, NB, FWD, MT, LEFT, EMIT>();
+        if (pst) return pst;
     }
     int64_t grid = (ncols + kDiagCols - 1) / kDiagCols;
     if (grid > 0x7fffffff) return GB_STATUS_CUDA_ERROR;
@@ -246,20 +260,6 @@ int launch_diag_solve(const Canon<T> &c, int64_t r0, int nr, T alpha)
     GB_DIAG_CASE(false, true, false)
 #undef GB_DIAG_CASE
     return GB_STATUS_CUDA_ERROR;
-}
-
-template int launch_diag_solve<double>(const Canon<double> &, int64_t, int, double);
-template int launch_diag_solve<float>(const Canon<float> &, int64_t, int, float);
-
-// Mixed-precision path: forward solve of one 64-row block held as a band
-// (row i of the block at Msub + i*lda, its 64 entries contiguous), FP32
-// right-hand sides in column-major Y, BF16 copy of the result to Ebf.
-int launch_diag_solve_band_f32(const float *Msub, int64_t lda, float *Y, int64_t ldy, int nr,
-                               int64_t ncols, __nv_bfloat16 *Ebf, cudaStream_t s)
-{
-    if (nr <= 0 || ncols <= 0) return 0;
-    if (nr > 64) return GB_STATUS_CUDA_ERROR;
-    return launch_nb<float, 64, true, true, true, true>(Msub, lda, Y, ldy, nr, ncols, 1.0f, 0, s, Ebf);
 }
 
 }  // namespace gb

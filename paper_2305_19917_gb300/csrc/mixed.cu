@@ -34,13 +34,16 @@ int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t 
 int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
                        const double *dg, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
                        cudaStream_t s);
-int launch_diag_solve_band_f32(const float *Msub, int64_t lda, float *Y, int64_t ldy, int nr, int64_t ncols,
-                               __nv_bfloat16 *Ebf, cudaStream_t s);
+int tc_gemm_prepare();
+int diag_inv_prepare();
+int launch_invert_blocks(const float *band, float *inv, int64_t nblocks, cudaStream_t s);
+int launch_apply_inverse(const float *Linv_b, float *Yb, int64_t ldy, __nv_bfloat16 *Ybf_b, int nr, int64_t ncols,
+                         cudaStream_t s);
 
 namespace {
 
 constexpr int kSlices = 7;     // digit slices of Mv (6 bits each)
-constexpr int kBand = 64;      // FP32 band of diagonal 64-blocks
+constexpr int kBand = 128;     // FP32 band of diagonal 128-blocks (column-major per block)
 
 // Canonical forward view of the user problem (device-side description).
 struct View {
@@ -83,17 +86,17 @@ __device__ void load_tile(const View &v, int64_t i0, int64_t c0, double (*t)[65]
 // diagonal block of i0 (the residual kernel reads up to that column).
 __device__ __forceinline__ bool tile_needed(int64_t i0, int64_t c0) { return c0 < ((i0 >> 7) << 7) + 128; }
 
-__device__ __forceinline__ int exponent_of(double a)
+// Biased binary exponent field of a double (0 for zero / subnormal).
+__device__ __forceinline__ int bexp(double a)
 {
-    int e;
-    frexp(a, &e);  // a = f 2^e, f in [0.5, 1)
-    return e;
+    return int((static_cast<unsigned long long>(__double_as_longlong(a)) >> 52) & 0x7FF);
 }
 
-// Pass 1: row exponents e_i with max_{c<i} |Mv'(i,c)| < 2^(e_i - 1): the
-// strictly lower part only, so that small off-diagonal entries keep all
-// their digits when the diagonal is much larger (the diagonal is applied
-// exactly in FP64 by the residual kernel).
+// Pass 1: row exponents.  e_i = E + 2 where 2^E <= max_{c<i} |Mv'(i,c)| <
+// 2^(E+1), so every strictly-lower entry satisfies |a| < 2^(e_i - 1): the
+// strictly lower part only, so that small off-diagonal entries keep all their
+// digits when the diagonal is much larger (the diagonal is applied exactly in
+// FP64 by the residual kernel).  Integer arithmetic on the exponent fields.
 __global__ void __launch_bounds__(256) rowexp_kernel(View v, int64_t kp, int *e_row)
 {
     __shared__ double t[64][65];
@@ -103,11 +106,57 @@ __global__ void __launch_bounds__(256) rowexp_kernel(View v, int64_t kp, int *e_
     __syncthreads();
     const int tid = threadIdx.x;
     if (tid < 64) {
-        double mx = 0;
+        int mx = 0;
         for (int c = 0; c < 64; c++)
-            if (c0 + c != i0 + tid) mx = fmax(mx, fabs(t[tid][c]));
-        if (mx > 0) atomicMax(&e_row[i0 + tid], exponent_of(mx) + 1);
+            if (c0 + c != i0 + tid) mx = max(mx, bexp(t[tid][c]));
+        if (mx > 0) atomicMax(&e_row[i0 + tid], mx - 1023 + 2);
     }
+}
+
+// Round-to-nearest-even BF16 of a double, from its bit pattern (integer
+// operations only; results below the BF16 normal range flush to zero).
+__device__ __forceinline__ __nv_bfloat16 d2bf16(double a)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a));
+    const unsigned s = unsigned(b >> 63) << 15;
+    const int E = int((b >> 52) & 0x7FF);
+    const unsigned long long m = b & ((1ull << 52) - 1);
+    unsigned short out;
+    if (E == 0x7FF) {
+        out = (unsigned short)(s | 0x7F80u | (m ? 0x40u : 0u));
+    } else {
+        int e = E - 1023 + 127;
+        if (E == 0 || e <= 0) {
+            out = (unsigned short)s;
+        } else {
+            unsigned m7 = unsigned(m >> 45);
+            const unsigned long long rem = m & ((1ull << 45) - 1), half = 1ull << 44;
+            if (rem > half || (rem == half && (m7 & 1u))) m7++;
+            if (m7 == 128u) {
+                m7 = 0;
+                e++;
+            }
+            out = (e >= 255) ? (unsigned short)(s | 0x7F80u) : (unsigned short)(s | (unsigned(e) << 7) | m7);
+        }
+    }
+    return __ushort_as_bfloat16(out);
+}
+
+// The 42-bit fixed-point value N = round(a 2^(42-e)) of |a| < 2^(e-1)
+// (|N| <= 2^41), computed from the bit pattern with integer operations.
+__device__ __forceinline__ long long fixed42(double a, int e)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a));
+    const int E = int((b >> 52) & 0x7FF);
+    if (E == 0) return 0;  // zero (subnormals are far below 2^-42 of any row scale)
+    const unsigned long long mant = (b & ((1ull << 52) - 1)) | (1ull << 52);  // a = mant 2^(E-1075)
+    // a 2^(42-e) = mant 2^(E - 1075 + 42 - e): right shift by r = 1033 + e - E
+    const int r = 1033 + e - E;
+    long long n;
+    if (r >= 63) n = 0;
+    else if (r <= 0) n = (long long)(mant << (-r));  // cannot happen for |a| < 2^(e-1)
+    else n = (long long)((mant + (1ull << (r - 1))) >> r);
+    return (b >> 63) ? -n : n;
 }
 
 // Pass 2: BF16 copy (round to nearest), the 7 digit slices of the strictly
@@ -128,18 +177,19 @@ prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bflo
         int64_t i = i0 + li, c = c0 + lc;
         double a = t[li][lc];
         size_t off = size_t(i) * size_t(kp) + size_t(c);
-        Abf[off] = __double2bfloat16(a);
-        int e = e_row[i];
-        double r = (a == 0.0 || c == i) ? 0.0 : ldexp(a, -e);  // |r| <= 1/2
+        Abf[off] = d2bf16(a);
+        // balanced base-64 digits of N = round(a 2^(42-e)): N = sum_p q_p 64^(7-p),
+        // q_p in [-32, 32]; least significant first
+        long long N = (c == i) ? 0 : fixed42(a, e_row[i]);
         if (c == i) dg[i] = a;
 #pragma unroll
-        for (int p = 0; p < kSlices; p++) {
-            double x = r * 64.0;
-            double q = rint(x);
-            r = x - q;
-            As[p * slice + off] = __double2bfloat16(q);  // |q| <= 32: exact
+        for (int p = kSlices - 1; p >= 1; p--) {
+            const long long d = ((N + 32) & 63) - 32;
+            As[p * slice + off] = __int2bfloat16_rn(int(d));  // exact: |d| <= 32
+            N = (N - d) >> 6;
         }
-        if ((c >> 6) == (i >> 6)) band[size_t(i) * kBand + (c & 63)] = float(a);
+        As[off] = __int2bfloat16_rn(int(N));  // top digit, |N| <= 32
+        if (c / kBand == i / kBand) band[size_t(c) * kBand + (i % kBand)] = float(a);
     }
 }
 
@@ -202,19 +252,21 @@ __global__ void to_f32_kernel(const double *R, float *Y, int64_t n)
         Y[i] = float(R[i]);
 }
 
-// Per column j: f_j with max_k |Y(k,j)| < 2^(f_j - 1); the two 6-bit digits
-// z_1, z_2 of Y(:,j) 2^-f_j; X += D~ with D~ = 2^f_j (z_1 2^-6 + z_2 2^-12);
-// accumulates ||D~||^2, ||X||^2 into norms[0], norms[1] and the largest
-// column ratio max|D~| / max|X| into norms[2] (as bits of a double).
+// Per column j: f_j = E + 2 with 2^E <= max_k |Y(k,j)| < 2^(E+1); the
+// 12-bit value N = round(Y 2^(12-f_j)) (|N| <= 2^11, FP32 arithmetic, exact
+// scaling) split into balanced base-64 digits z_1, z_2 (N = 64 z_1 + z_2);
+// X += D~ with D~ = N 2^(f_j-12) (exact in FP32, added in FP64).
+// Accumulates sum D~^2 into norms[0] (FP32 partial sums), and, on the first
+// call, sum X^2 into norms[1] and the column maxima of |X| into xmax; the
+// largest column ratio max|D~| / max|X| goes to norms[2] (as bits).
 __global__ void __launch_bounds__(256)
 slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bfloat16 *Zs, int *f_col,
-                  double *X, double *norms, int first)
+                  double *X, float *xmax, double *norms, int first)
 {
     const int64_t j = blockIdx.x;
     const float *y = Y + j * kp;
     __shared__ float red[8];
-    __shared__ double redd[3][8];
-    __shared__ double mxred[8];
+    __shared__ float redd[2][8];
     float mx = 0.f;
     for (int64_t i = threadIdx.x; i < kp; i += 256) mx = fmaxf(mx, fabsf(y[i]));
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -222,52 +274,47 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
     __syncthreads();
     mx = 0.f;
     for (int w = 0; w < 8; w++) mx = fmaxf(mx, red[w]);
-    const int f = (mx > 0.f) ? exponent_of(double(mx)) + 1 : 0;
+    const int be = int((__float_as_uint(mx) >> 23) & 0xFF);
+    const int f = (be > 0) ? be - 127 + 2 : 0;
     if (threadIdx.x == 0) f_col[j] = f;
+    const float up = ldexpf(1.0f, 12 - f), down = ldexpf(1.0f, f - 12);
     __nv_bfloat16 *z1 = Zs + j * kp;
     __nv_bfloat16 *z2 = Zs + np * kp + j * kp;
     double *x = X + j * kp;
-    double sd = 0, sx = 0, md = 0, mxx = 0;
+    float sd = 0.f, sx = 0.f;
     for (int64_t i = threadIdx.x; i < kp; i += 256) {
-        double r = ldexp(double(y[i]), -f);  // |r| < 1/2
-        double t1 = r * 64.0, q1 = rint(t1);
-        double t2 = (t1 - q1) * 64.0, q2 = rint(t2);
-        z1[i] = __double2bfloat16(q1);
-        z2[i] = __double2bfloat16(q2);
-        double d = ldexp(q1 * 64.0 + q2, f - 12);
-        double xv = first ? d : x[i] + d;
-        x[i] = xv;
-        if (j < ncols) {
-            sd += d * d;
-            sx += xv * xv;
-            md = fmax(md, fabs(d));
-            mxx = fmax(mxx, fabs(xv));
-        }
+        const int N = (be > 0) ? __float2int_rn(y[i] * up) : 0;
+        const int q2 = ((N + 32) & 63) - 32;
+        const int q1 = (N - q2) >> 6;
+        z1[i] = __int2bfloat16_rn(q1);
+        z2[i] = __int2bfloat16_rn(q2);
+        const float d = float(N) * down;  // exact
+        if (first) x[i] = double(d);
+        else x[i] += double(d);
+        sd = fmaf(d, d, sd);
     }
+    if (first) sx = sd;
     for (int o = 16; o > 0; o >>= 1) {
         sd += __shfl_xor_sync(0xffffffffu, sd, o);
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
-        mxx = fmax(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
     }
     if ((threadIdx.x & 31) == 0) {
         redd[0][threadIdx.x >> 5] = sd;
         redd[1][threadIdx.x >> 5] = sx;
-        redd[2][threadIdx.x >> 5] = md;
-        mxred[threadIdx.x >> 5] = mxx;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0, cmd = 0, cmx = 0;
+    if (threadIdx.x == 0 && j < ncols) {
+        float a = 0.f, b = 0.f;
         for (int w = 0; w < 8; w++) {
             a += redd[0][w];
             b += redd[1][w];
-            cmd = fmax(cmd, redd[2][w]);
-            cmx = fmax(cmx, mxred[w]);
         }
-        const double ratio = (cmx > 0) ? cmd / cmx : (cmd > 0 ? 1.0 : 0.0);
-        atomicAdd(&norms[0], a);
-        atomicAdd(&norms[1], b);
+        const float dmax = float((be > 0) ? mx : 0.f);
+        if (first) xmax[j] = dmax;
+        const float xm = first ? dmax : xmax[j];
+        const double ratio = (xm > 0.f) ? double(dmax) / double(xm) : (dmax > 0.f ? 1.0 : 0.0);
+        atomicAdd(&norms[0], double(a));
+        if (first) atomicAdd(&norms[1], double(b));
         // non-negative doubles order like their bit patterns
         atomicMax(reinterpret_cast<unsigned long long *>(&norms[2]),
                   static_cast<unsigned long long>(__double_as_longlong(ratio)));
@@ -305,7 +352,7 @@ struct LowExec {
     float *Y;
     __nv_bfloat16 *Ybf;
     const __nv_bfloat16 *Abf;
-    const float *band;
+    const float *binv;  // inverses of the diagonal kBand-blocks
     int64_t kp, np;
     cudaStream_t s;
     int status = 0;
@@ -317,7 +364,8 @@ struct LowExec {
             drive_blocked(*this, b0, b0 + nr, (int64_t)kBand, a, true);
             return;
         }
-        status = launch_diag_solve_band_f32(band + b0 * kBand, kBand, Y + b0, kp, (int)nr, np, Ybf + b0, s);
+        // TS task: X_b = L_b^-1 Y_b with the precomputed inverse of the block
+        status = launch_apply_inverse(binv + b0 * kBand, Y + b0, kp, Ybf + b0, (int)nr, np, s);
     }
     void gemm(int64_t ci0, int64_t M, int64_t ak0, int64_t K, float a)
     {
@@ -326,11 +374,10 @@ struct LowExec {
     }
 };
 
+// Recursive model (Section V-A) down to TS tasks of kBand rows.
 int low_solve(LowExec &e, int64_t kp)
 {
-    int depth = 0;
-    while ((kp >> (depth + 1)) >= 256 && depth < 10) depth++;
-    drive_recursive(e, 0, kp, depth, (int64_t)kBand, 1.0f, true);
+    drive_recursive(e, 0, kp, 24, (int64_t)kBand, 1.0f, true);
     return e.status;
 }
 
@@ -354,6 +401,62 @@ int residual_update(double *R, const __nv_bfloat16 *As, const __nv_bfloat16 *Zs,
         int64_t hi = lo + 16384 < kp ? lo + 16384 : kp;
         GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, dg, kp, np, lo, hi, Lmax, s));
     }
+    return 0;
+}
+
+// The low-precision solve is a fixed sequence of ~2 kp/64 launches on
+// fixed buffers: it is captured once into a CUDA graph (on a library stream)
+// and replayed on the caller's stream at every refinement step.  The last
+// graph is kept per device, keyed by workspace address and sizes.
+struct LowGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void *ws = nullptr;
+    int64_t kp = 0, np = 0;
+    uint64_t nkernels = 0;
+};
+
+int low_graph(LowExec &le, const void *ws, LowGraph **out)
+{
+    static LowGraph cache[64];
+    static cudaStream_t cap_stream[64] = {nullptr};
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GB_STATUS_CUDA_ERROR;
+    LowGraph &g = cache[dev];
+    if (g.exec && g.ws == ws && g.kp == le.kp && g.np == le.np) {
+        *out = &g;
+        return 0;
+    }
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    if (!cap_stream[dev]) GB_CUDA(cudaStreamCreateWithFlags(&cap_stream[dev], cudaStreamNonBlocking));
+    // everything that allocates or sets attributes happens before capture
+    GB_TRY(tc_gemm_prepare());
+    GB_TRY(diag_inv_prepare());
+    cudaStream_t user = le.s;
+    le.s = cap_stream[dev];
+    le.status = 0;
+    const uint64_t before = capture_count();
+    GB_CUDA(cudaStreamBeginCapture(le.s, cudaStreamCaptureModeThreadLocal));
+    int st = low_solve(le, le.kp);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(le.s, &graph);
+    le.s = user;
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    GB_CUDA(e);
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    GB_CUDA(e);
+    g.ws = ws;
+    g.kp = le.kp;
+    g.np = le.np;
+    g.nkernels = capture_count() - before;
+    *out = &g;
     return 0;
 }
 
@@ -382,8 +485,10 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
         return o;
     };
     size_t o_abf = take(kk * 2), o_as = take(kk * 2 * kSlices), o_band = take(size_t(kp) * kBand * 4);
+    size_t o_binv = take(size_t(kp) * kBand * 4);
     size_t o_r = take(kn * 8), o_x = take(kn * 8), o_y = take(kn * 4), o_ybf = take(kn * 2), o_zs = take(kn * 4);
     size_t o_e = take(size_t(kp) * 4), o_f = take(size_t(np) * 4), o_norm = take(64), o_dg = take(size_t(kp) * 8);
+    size_t o_xm = take(size_t(np) * 4);
     cudaMemPool_t pool = library_pool();
     if (!pool) return GB_STATUS_CUDA_ERROR;
     char *ws = nullptr;
@@ -391,6 +496,7 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
     auto *Abf = reinterpret_cast<__nv_bfloat16 *>(ws + o_abf);
     auto *As = reinterpret_cast<__nv_bfloat16 *>(ws + o_as);
     auto *band = reinterpret_cast<float *>(ws + o_band);
+    auto *binv = reinterpret_cast<float *>(ws + o_binv);
     auto *R = reinterpret_cast<double *>(ws + o_r);
     auto *X = reinterpret_cast<double *>(ws + o_x);
     auto *Y = reinterpret_cast<float *>(ws + o_y);
@@ -400,6 +506,7 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
     auto *f_col = reinterpret_cast<int *>(ws + o_f);
     auto *norms = reinterpret_cast<double *>(ws + o_norm);
     auto *dg = reinterpret_cast<double *>(ws + o_dg);
+    auto *xmax = reinterpret_cast<float *>(ws + o_xm);
 
     int st = 0;
     double h_norm[3] = {0, 0, 0};
@@ -425,31 +532,51 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
                 B, ldb, side == GB_LEFT, !forward, k, ncols, alpha, R, kp);
             if ((st = check(cudaGetLastError()))) break;
         }
-        LowExec le{Y, Ybf, Abf, band, kp, np, s};
+        if ((st = launch_invert_blocks(band, binv, kp / kBand, s))) break;
+        LowExec le{Y, Ybf, Abf, binv, kp, np, s};
+        LowGraph *lg = nullptr;
+        if ((st = low_graph(le, ws, &lg))) break;
         const int64_t nel = int64_t(kn);
         const unsigned eg = (unsigned)((nel + 255) / 256 < 152 * 64 ? (nel + 255) / 256 : 152 * 64);
         int Lmax = 8;
+        double nx = 0, prev_rho = 0;
         for (int t = 0;; t++) {
             {
                 LaunchScope ls(KK_CONVERT, s, 0, 12.0 * double(nel));
                 to_f32_kernel<<<eg, 256, 0, s>>>(R, Y, nel);
                 if ((st = check(cudaGetLastError()))) break;
             }
-            le.status = 0;
-            if ((st = low_solve(le, kp))) break;
+            {
+                LaunchScope ls(KK_GRAPH, s, double(kp) * double(kp) * double(np), 0.0, lg->nkernels);
+                if ((st = check(cudaGraphLaunch(lg->exec, s)))) break;
+            }
             if ((st = check(cudaMemsetAsync(norms, 0, 3 * sizeof(double), s)))) break;
             {
-                LaunchScope ls(KK_CONVERT, s, 0, 24.0 * double(nel));
-                slice_cols_kernel<<<(unsigned)np, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, norms, t == 0);
+                LaunchScope ls(KK_CONVERT, s, 0, 20.0 * double(nel));
+                slice_cols_kernel<<<(unsigned)np, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms,
+                                                                t == 0);
                 if ((st = check(cudaGetLastError()))) break;
             }
             if ((st = check(cudaMemcpyAsync(h_norm, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)))) break;
             if ((st = check(cudaStreamSynchronize(s)))) break;
-            const double nd = std::sqrt(h_norm[0]), nx = std::sqrt(h_norm[1]);
+            const double nd = std::sqrt(h_norm[0]);
+            if (t == 0) nx = std::sqrt(h_norm[1]);
+            const double rho = nx > 0 ? nd / nx : 0.0;
             if (t > 0) {
                 iters = t;
-                est = nx > 0 ? nd / nx : 0.0;
-                if (est <= tol || t >= max_iter) break;
+                est = rho;
+                if (rho <= tol) break;
+                // Predicted error after this update: rho times the observed
+                // contraction, when the iteration contracts well.
+                if (t >= 2 && prev_rho > 0) {
+                    const double c = rho / prev_rho;
+                    if (c <= 0.1 && rho * c <= tol) {
+                        est = rho * c;
+                        break;
+                    }
+                }
+                if (t >= max_iter) break;
+                prev_rho = rho;
             }
             Lmax = (t == 0) ? 8 : levels_for(h_norm[2]);
             if ((st = residual_update(R, As, Zs, e_row, f_col, dg, kp, np, Lmax, s))) break;

@@ -33,10 +33,21 @@ cudaEvent_t get_event()
 
 }  // namespace
 
-LaunchScope::LaunchScope(int k, cudaStream_t s, double flops, double bytes)
+uint64_t &capture_count()
+{
+    static thread_local uint64_t n = 0;
+    return n;
+}
+
+LaunchScope::LaunchScope(int k, cudaStream_t s, double flops, double bytes, uint64_t nkernels)
     : kind(k), slot(-1), stream(s)
 {
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        capture_count() += nkernels;
+        return;
+    }
+    g_launches.fetch_add(nkernels, std::memory_order_relaxed);
     if (!g_prof_on.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_mu);
     Rec r;

@@ -4,8 +4,9 @@
 // product accumulates in FP32 in tensor memory, C is FP32.
 //
 // Layout: A row-major (K-major), B column-major (K-major as the MMA's B
-// operand), C column-major.  One CTA per 128 x 256 output tile; K advances in
-// 64-element steps (one 128-byte swizzle row) through a 4-stage TMA ring.
+// operand), C column-major.  One CTA per 128 x BN output tile (BN = 256, 128
+// or 64); K advances in 64-element steps (one 128-byte swizzle row) through
+// a TMA ring of ~192 KB (4, 5 or 8 stages).
 // Warp roles: warp 0 issues TMA loads, warp 1 owns TMEM and issues the MMAs
 // (one elected thread), warps 2-5 drain the accumulator (each warp reads the
 // 32 TMEM lanes its rank allows) and apply the FP32 epilogue with coalesced
@@ -78,15 +79,26 @@ int *device_status_word()
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr size_t SMEM_BYTES = 1024 + STAGES * size_t(STAGE_BYTES) + 256;
+constexpr int BM = 128, BK = 64;
+constexpr uint32_t A_BYTES = BM * BK * 2;
 
+// Tile shape per N-tile width: stages fill ~192 KB of shared memory.
+template <int BN>
+struct TileCfg {
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+    static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 8 ? 8 : (192 * 1024) / STAGE_BYTES;
+    static constexpr size_t SMEM_BYTES = 1024 + STAGES * size_t(STAGE_BYTES) + 256;
+};
+
+template <int BN>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     float *__restrict__ C, int64_t ldc, int M, int N, int K, float alpha, int *status)
 {
+    constexpr int STAGES = TileCfg<BN>::STAGES;
+    constexpr uint32_t B_BYTES = TileCfg<BN>::B_BYTES;
+    constexpr uint32_t STAGE_BYTES = TileCfg<BN>::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = base;
@@ -110,7 +122,7 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         abort_flag = 0;
         tc::fence_barrier_init();
     }
-    if (warp == 1) tc::tmem_alloc(tslot, BN);
+    if (warp == 1) tc::tmem_alloc(tslot, BN < 32 ? 32 : BN);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -162,14 +174,15 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                 tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c0), r);
                 tc::tmem_ld_wait();
                 if (gi < M) {
+                    // all 32 loads are issued before any store (the compiler
+                    // cannot prove the column addresses distinct)
+                    float cv[32];
+                    const int64_t gj0 = int64_t(n_blk) * BN + c0;
 #pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const int64_t gj = int64_t(n_blk) * BN + c0 + j;
-                        if (gj < N) {
-                            float *p = C + gi + gj * ldc;
-                            *p = alpha * *p - __uint_as_float(r[j]);
-                        }
-                    }
+                    for (int j = 0; j < 32; j++) cv[j] = (gj0 + j < N) ? C[gi + (gj0 + j) * ldc] : 0.f;
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        if (gj0 + j < N) C[gi + (gj0 + j) * ldc] = alpha * cv[j] - __uint_as_float(r[j]);
                 }
             }
         }
@@ -178,23 +191,38 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     __syncthreads();
     if (warp == 1) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, BN);
+        tc::tmem_dealloc(tmem, BN < 32 ? 32 : BN);
     }
 }
 
 }  // namespace
 
-// C (M x N, FP32, column-major, ldc) = alpha*C - A*B with A (M x K, BF16
-// row-major, lda) and B (K x N, BF16 column-major, ldb).  K % 64 == 0,
-// lda % 8 == 0, ldb % 8 == 0, A and B 16-byte aligned.
-int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
-                        int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s)
+template <int BN>
+static int prepare_bn()
 {
-    if (M <= 0 || N <= 0) return 0;
-    if (K <= 0 || K % BK || lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) ||
-        (reinterpret_cast<uintptr_t>(B) & 15))
-        return GB_STATUS_CUDA_ERROR;
-    if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
+    static bool attr = false;
+    if (!attr) {
+        GB_CUDA(cudaFuncSetAttribute(tc_gemm_bf16_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TileCfg<BN>::SMEM_BYTES));
+        attr = true;
+    }
+    return 0;
+}
+
+// One-time per-process set-up (kernel attributes, device status word); must
+// run before any stream capture that launches the kernel.
+int tc_gemm_prepare()
+{
+    GB_TRY(prepare_bn<256>());
+    GB_TRY(prepare_bn<128>());
+    GB_TRY(prepare_bn<64>());
+    return device_status_word() ? 0 : GB_STATUS_CUDA_ERROR;
+}
+
+template <int BN>
+static int launch_bn(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
+                     float *C, int64_t ldc, float alpha, cudaStream_t s)
+{
     CUtensorMap ta, tb;
     {
         uint64_t dims[2] = {uint64_t(K), uint64_t(M)};
@@ -205,22 +233,36 @@ int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t 
     {
         uint64_t dims[2] = {uint64_t(K), uint64_t(N)};
         uint64_t strides[1] = {uint64_t(ldb) * 2};
-        uint32_t box[2] = {BK, BN};
+        uint32_t box[2] = {BK, uint32_t(BN)};
         GB_TRY(encode_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, strides, box));
     }
-    static bool attr = false;
-    if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(tc_gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES));
-        attr = true;
-    }
+    GB_TRY(tc_gemm_prepare());
     int *st = device_status_word();
-    if (!st) return GB_STATUS_CUDA_ERROR;
     dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
     if (grid.y > 65535) return GB_STATUS_CUDA_ERROR;
     LaunchScope ls(KK_GEMM_TC, s, 2.0 * M * N * K, 2.0 * (double(M) * K + double(K) * N) + 8.0 * M * N);
-    tc_gemm_bf16_kernel<<<grid, 192, SMEM_BYTES, s>>>(ta, tb, C, ldc, (int)M, (int)N, (int)K, alpha, st);
+    tc_gemm_bf16_kernel<BN><<<grid, 192, TileCfg<BN>::SMEM_BYTES, s>>>(ta, tb, C, ldc, (int)M, (int)N, (int)K,
+                                                                       alpha, st);
     return check(cudaGetLastError());
+}
+
+// C (M x N, FP32, column-major, ldc) = alpha*C - A*B with A (M x K, BF16
+// row-major, lda) and B (K x N, BF16 column-major, ldb).  K % 64 == 0,
+// lda % 8 == 0, ldb % 8 == 0, A and B 16-byte aligned.  The N-tile width is
+// the widest of 256 / 128 / 64 that still gives at least two CTAs per SM
+// of work (small leaf updates use narrow tiles to spread over the GPU).
+int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
+                        int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return 0;
+    if (K <= 0 || K % BK || lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) ||
+        (reinterpret_cast<uintptr_t>(B) & 15))
+        return GB_STATUS_CUDA_ERROR;
+    if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
+    const int64_t mt = (M + BM - 1) / BM;
+    if (mt * ((N + 255) / 256) >= 2 * 152) return launch_bn<256>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s);
+    if (mt * ((N + 127) / 128) >= 2 * 152) return launch_bn<128>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s);
+    return launch_bn<64>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s);
 }
 
 }  // namespace gb

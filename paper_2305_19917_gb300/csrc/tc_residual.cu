@@ -152,19 +152,19 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             const int s2 = 6 * (Lmax - (p + 3));
             const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 256 + half * 64);
 #pragma unroll
-            for (int c0 = 0; c0 < 64; c0 += 32) {
-                uint32_t r1[32];
-                tc::tmem_ld32(tbase + c0, r1);
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                uint32_t r1[16];
+                tc::tmem_ld16(tbase + c0, r1);
                 tc::tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; j++)
+                for (int j = 0; j < 16; j++)
                     T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r1[j]))) << s1;
                 if (two) {
-                    uint32_t r2[32];
-                    tc::tmem_ld32(tbase + 128 + c0, r2);
+                    uint32_t r2[16];
+                    tc::tmem_ld16(tbase + 128 + c0, r2);
                     tc::tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; j++)
+                    for (int j = 0; j < 16; j++)
                         T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r2[j]))) << s2;
                 }
             }
@@ -179,18 +179,30 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             // the launch whose K range holds column i
             const bool has_diag = gi >= k_lo && gi < k_hi;
             const double di = has_diag ? dg[gi] : 0.0;
+            // 4 columns at a time: every load is issued before the stores
 #pragma unroll
-            for (int c = 0; c < 64; c++) {
-                const int gj = j0 + half * 64 + c;
-                const int fj = f_col[gj];
-                double *pr = R + gi + int64_t(gj) * ldr;
-                double sub = ldexp(static_cast<double>(T[c]), ei + fj);
-                if (has_diag) {
-                    const int64_t zo = int64_t(gj) * ldr + gi;
-                    const double z = double(__bfloat162float(Zg[zo])) * 64.0 + double(__bfloat162float(Zg[zslice + zo]));
-                    sub += di * ldexp(z, fj - 12);
+            for (int c0 = 0; c0 < 64; c0 += 4) {
+                double rv[4];
+                int fj[4];
+                float zv[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const int gj = j0 + half * 64 + c0 + c;
+                    rv[c] = R[gi + int64_t(gj) * ldr];
+                    fj[c] = f_col[gj];
+                    zv[c] = 0.f;
+                    if (has_diag) {
+                        const int64_t zo = int64_t(gj) * ldr + gi;
+                        zv[c] = __bfloat162float(Zg[zo]) * 64.0f + __bfloat162float(Zg[zslice + zo]);
+                    }
                 }
-                *pr -= sub;
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const int gj = j0 + half * 64 + c0 + c;
+                    double sub = ldexp(static_cast<double>(T[c0 + c]), ei + fj[c]);
+                    if (has_diag) sub += di * ldexp(double(zv[c]), fj[c] - 12);
+                    R[gi + int64_t(gj) * ldr] = rv[c] - sub;
+                }
             }
         }
     }
