@@ -227,6 +227,20 @@ __host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N)
            | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
+// Grouped rasterisation of a linear CTA index over an nM x nN tile grid:
+// G consecutive row tiles are swept across all column tiles before the next
+// group, so the CTAs resident at one time share both operands in L2.
+// (Without it a wave of 152 CTAs spans ~1 row tile and re-streams the whole
+// B operand per row tile from HBM.)
+__device__ __forceinline__ void raster_grouped(int idx, int nM, int nN, int G, int &m, int &n)
+{
+    const int g = idx / (G * nN);
+    const int rows = min(G, nM - g * G);
+    const int r = idx - g * G * nN;
+    m = g * G + r % rows;
+    n = r / rows;
+}
+
 }  // namespace tc
 
 // Host: encode a 2-D / 3-D tiled tensor map with 128-byte swizzle

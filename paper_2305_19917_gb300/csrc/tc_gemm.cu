@@ -94,7 +94,8 @@ struct TileCfg {
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                    float *__restrict__ C, int64_t ldc, int M, int N, int K, float alpha, int *status)
+                    float *__restrict__ C, int64_t ldc, int M, int N, int K, float alpha, int nMt, int nNt,
+                    int *status)
 {
     constexpr int STAGES = TileCfg<BN>::STAGES;
     constexpr uint32_t B_BYTES = TileCfg<BN>::B_BYTES;
@@ -110,7 +111,8 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m_blk = blockIdx.y, n_blk = blockIdx.x;
+    int m_blk, n_blk;
+    tc::raster_grouped(int(blockIdx.x), nMt, nNt, 8, m_blk, n_blk);
     const int nk = K / BK;
 
     if (threadIdx.x == 0) {
@@ -238,11 +240,13 @@ static int launch_bn(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda
     }
     GB_TRY(tc_gemm_prepare());
     int *st = device_status_word();
-    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
-    if (grid.y > 65535) return GB_STATUS_CUDA_ERROR;
+    // 1-D grid (grouped rasterisation)
+    const int64_t nM = (M + BM - 1) / BM, nN = (N + BN - 1) / BN;
+    if (nM > 65535 || nN > 65535 || nM * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
+    dim3 grid((unsigned)(nM * nN));
     LaunchScope ls(KK_GEMM_TC, s, 2.0 * M * N * K, 2.0 * (double(M) * K + double(K) * N) + 8.0 * M * N);
     tc_gemm_bf16_kernel<BN><<<grid, 192, TileCfg<BN>::SMEM_BYTES, s>>>(ta, tb, C, ldc, (int)M, (int)N, (int)K,
-                                                                       alpha, st);
+                                                                       alpha, (int)nM, (int)nN, st);
     return check(cudaGetLastError());
 }
 

@@ -42,7 +42,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                    double *__restrict__ R, int64_t ldr, const int *__restrict__ e_row,
                    const int *__restrict__ f_col, const double *__restrict__ dg,
                    const __nv_bfloat16 *__restrict__ Zg, int64_t zslice, int k_lo, int k_hi, int Lmax,
-                   int *status)
+                   int nMt, int nNt, int *status)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -56,8 +56,9 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m_blk = gridDim.y - 1 - blockIdx.y;  // longest K ranges first
-    const int n_blk = blockIdx.x;
+    int mg, n_blk;
+    tc::raster_grouped(int(blockIdx.x), nMt, nNt, 8, mg, n_blk);
+    const int m_blk = nMt - 1 - mg;  // longest K ranges first
     const int i0 = m_blk * BM, j0 = n_blk * BNO;
     const int k_end = min(k_hi, i0 + BM);
     if (k_end <= k_lo) return;  // tile entirely above the diagonal: nothing to add
@@ -249,8 +250,10 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
     }
     int *st = device_status_word();
     if (!st) return GB_STATUS_CUDA_ERROR;
-    dim3 grid((unsigned)(np / BNO), (unsigned)(kp / BM));
-    if (grid.y > 65535) return GB_STATUS_CUDA_ERROR;
+    // 1-D grid of nM*nN CTAs (grouped rasterisation)
+    const int64_t nM = kp / BM, nN = np / BNO;
+    if (nM > 65535 || nN > 65535 || nM * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
+    dim3 grid((unsigned)(nM * nN));
     // algorithmic work: (Lmax-1) passes over the lower triangle of the K range
     double tri = 0;
     for (int64_t i0 = 0; i0 < kp; i0 += BM) {
@@ -262,7 +265,7 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
     LaunchScope ls(KK_RESIDUAL, s, flops, 16.0 * kp * np);
     tc_residual_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(
         ta, tz, R, ldr, e_row, f_col, dg, static_cast<const __nv_bfloat16 *>(Zs), np * kp, (int)k_lo, (int)k_hi,
-        Lmax, st);
+        Lmax, (int)nM, (int)nN, st);
     return check(cudaGetLastError());
 }
 
