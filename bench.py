@@ -245,7 +245,9 @@ def run_ours(args):
         B.copy_(B0)
 
     def solve_mixed():
-        return api.trsm_mixed(side, uplo, trans, diag, alpha, A, B, tol=tol, max_iter=max_iter, stream=stream)
+        st, it, est = api.trsm_mixed(side, uplo, trans, diag, alpha, A, B, tol=tol, max_iter=max_iter,
+                                     stream=stream)
+        return st, it, est, api.gb_mixed_history()
 
     def solve_fp64():
         api.trsm(side, uplo, trans, diag, alpha, A, B, stream=stream)
@@ -293,6 +295,7 @@ def run_ours(args):
             acc["refinement_steps"] = [o[1] for o in outs]
             acc["est_err"] = [o[2] for o in outs]
             acc["status"] = [o[0] for o in outs]
+            acc["history_rho_levels"] = outs[-1][3]
 
     # ---- e2e: host buffers, H2D + solve + D2H inside the timed region ----
     A_pin = torch.empty((m, m), dtype=torch.float64, pin_memory=True).t()

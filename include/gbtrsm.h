@@ -142,6 +142,15 @@ int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
                    int *iters_out, double *est_err_out, void *stream);
 
 /*
+ * gb_mixed_history: refinement history of the last gb_dtrsm_mixed call made
+ * by this host thread.  Writes up to `cap` entries: rho[t] = ||D||_F/||X||_F
+ * of correction t+1 and levels[t] = the number of 6-bit digit levels the
+ * residual preceding that correction used (either pointer may be NULL).
+ * Returns the number of corrections recorded.  Host only.
+ */
+int gb_mixed_history(double *rho, int *levels, int cap);
+
+/*
  * gb_plan_counts: host-only description of the launches a plan issues for a
  * triangle of order k (no GPU work).  Writes the number of diagonal-block
  * solves and of GEMM updates, and the sum over GEMMs of M*N*K / ncols (i.e.

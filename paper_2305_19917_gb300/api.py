@@ -50,6 +50,7 @@ _SIGS = {
     "gb_version": ([], i32),
     "gb_dtrsm_mixed": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32,
                         ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
+    "gb_mixed_history": ([ctypes.POINTER(dbl), ctypes.POINTER(i32), i32], i32),
     "gb_bf16_gemm_update": ([i64, i64, i64, vp, i64, vp, i64, vp, i64, flt, vp], i32),
     "gb_device_status": ([i32], i32),
     "gb_kernel_launches": ([], ctypes.c_uint64),
@@ -123,6 +124,14 @@ def gb_dtrsm_mixed(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, pr
     st = lib().gb_dtrsm_mixed(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
                               ctypes.byref(it), ctypes.byref(est), stream or None)
     return st, it.value, est.value
+
+
+def gb_mixed_history(cap=64):
+    """[(rho_t, levels_t), ...] of the last mixed solve on this thread."""
+    rho = (dbl * cap)()
+    lev = (i32 * cap)()
+    n = lib().gb_mixed_history(rho, lev, cap)
+    return [(rho[i], lev[i]) for i in range(min(n, cap))]
 
 
 def trsm_mixed(side, uplo, trans, diag, alpha, A, B, tol=1e-11, prec=0, max_iter=30, stream=None):

@@ -32,7 +32,7 @@ namespace gb {
 int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
                         int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s);
 int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
-                       const double *dg, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
+                       const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
                        cudaStream_t s);
 int tc_gemm_prepare();
 int diag_inv_prepare();
@@ -197,7 +197,7 @@ prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bflo
 // Left: Bv(i,j) = B(i,j); Right: Bv(i,j) = B(j,i); reversal on i.
 __global__ void __launch_bounds__(256)
 prepB_kernel(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t ncols, double alpha,
-             double *R, int64_t kp)
+             double *R, float *Y, int64_t kp)
 {
     __shared__ double t[64][65];
     const int64_t i0 = int64_t(blockIdx.y) * 64, j0 = int64_t(blockIdx.x) * 64;
@@ -217,6 +217,7 @@ prepB_kernel(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64
     for (int idx = tid; idx < 64 * 64; idx += 256) {
         int li = idx & 63, lj = idx >> 6;
         R[(i0 + li) + (j0 + lj) * kp] = t[li][lj];
+        Y[(i0 + li) + (j0 + lj) * kp] = float(t[li][lj]);
     }
 }
 
@@ -243,13 +244,6 @@ writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t
             else B[j + r * ldb] = t[li][lj];
         }
     }
-}
-
-// Y = float(R), elementwise over kp x np (contiguous).
-__global__ void to_f32_kernel(const double *R, float *Y, int64_t n)
-{
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        Y[i] = float(R[i]);
 }
 
 // Per column j: f_j = E + 2 with 2^E <= max_k |Y(k,j)| < 2^(E+1); the
@@ -381,25 +375,28 @@ int low_solve(LowExec &e, int64_t kp)
     return e.status;
 }
 
-// Number of 6-bit digit levels the residual must keep for a correction whose
-// size relative to X is rho: the dropped pairs (weight 2^(-6(p+q))) must stay
-// below ~2^-44 of |Mv||X|.
-int levels_for(double rho)
+// Number of 6-bit digit levels the residual must keep for a correction Z
+// whose size relative to X is rho: level L terms (weight 2^(-6L)) sit
+// 2^(-6(L-2)) below the leading one, so dropping the levels above L costs
+// about rho 2^(-6(L-1)) |Mv||X|; that must stay below 2^-target |Mv||X| with
+// target = log2(1/tol) + 2 (a factor 4 under the requested tolerance).
+int levels_for(double rho, double tol)
 {
     if (!(rho > 0)) return 2;
-    double bits = -std::log2(rho);  // the correction is 2^-bits of X
-    int L = 8 - int(std::floor(bits / 6.0));
+    const double target = -std::log2(tol > 0 ? tol : 1e-16) + 2.0;
+    const double b = -std::log2(rho);
+    int L = int(std::ceil((target - b) / 6.0)) + 1;
     if (L > 8) L = 8;
     if (L < 2) L = 2;
     return L;
 }
 
 int residual_update(double *R, const __nv_bfloat16 *As, const __nv_bfloat16 *Zs, const int *e_row, const int *f_col,
-                    const double *dg, int64_t kp, int64_t np, int Lmax, cudaStream_t s)
+                    const double *dg, float *Y, int64_t kp, int64_t np, int Lmax, cudaStream_t s)
 {
     for (int64_t lo = 0; lo < kp; lo += 16384) {
         int64_t hi = lo + 16384 < kp ? lo + 16384 : kp;
-        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, dg, kp, np, lo, hi, Lmax, s));
+        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, dg, Y, kp, np, lo, hi, Lmax, s));
     }
     return 0;
 }
@@ -462,6 +459,12 @@ int low_graph(LowExec &le, const void *ws, LowGraph **out)
 
 }  // namespace
 
+// Per-thread record of the last mixed solve's refinement history:
+// rho_t = ||D_t||_F / ||X||_F for t = 1, 2, ... and the digit levels used.
+static thread_local double tl_rho[64];
+static thread_local int tl_levels[64];
+static thread_local int tl_nhist = 0;
+
 int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
                      int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
                      double *est_err_out, cudaStream_t s)
@@ -475,6 +478,7 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
     (void)prec;
 
     View v{A, lda, mt, !forward, diag == GB_UNIT, k};
+    tl_nhist = 0;
 
     // ---- workspace layout ----
     const size_t kk = size_t(kp) * size_t(kp), kn = size_t(kp) * size_t(np);
@@ -529,7 +533,7 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
         {
             LaunchScope ls(KK_CONVERT, s, 0, 16.0 * double(kp) * double(np));
             prepB_kernel<<<dim3((unsigned)(np / 64), (unsigned)(kp / 64)), 256, 0, s>>>(
-                B, ldb, side == GB_LEFT, !forward, k, ncols, alpha, R, kp);
+                B, ldb, side == GB_LEFT, !forward, k, ncols, alpha, R, Y, kp);
             if ((st = check(cudaGetLastError()))) break;
         }
         if ((st = launch_invert_blocks(band, binv, kp / kBand, s))) break;
@@ -537,15 +541,10 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
         LowGraph *lg = nullptr;
         if ((st = low_graph(le, ws, &lg))) break;
         const int64_t nel = int64_t(kn);
-        const unsigned eg = (unsigned)((nel + 255) / 256 < 152 * 64 ? (nel + 255) / 256 : 152 * 64);
         int Lmax = 8;
         double nx = 0, prev_rho = 0;
         for (int t = 0;; t++) {
-            {
-                LaunchScope ls(KK_CONVERT, s, 0, 12.0 * double(nel));
-                to_f32_kernel<<<eg, 256, 0, s>>>(R, Y, nel);
-                if ((st = check(cudaGetLastError()))) break;
-            }
+            // Y = float(R) was written by prepB (t = 0) or by the residual kernel
             {
                 LaunchScope ls(KK_GRAPH, s, double(kp) * double(kp) * double(np), 0.0, lg->nkernels);
                 if ((st = check(cudaGraphLaunch(lg->exec, s)))) break;
@@ -562,6 +561,11 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
             const double nd = std::sqrt(h_norm[0]);
             if (t == 0) nx = std::sqrt(h_norm[1]);
             const double rho = nx > 0 ? nd / nx : 0.0;
+            if (t > 0 && tl_nhist < 64) {
+                tl_rho[tl_nhist] = rho;
+                tl_levels[tl_nhist] = Lmax;
+                tl_nhist++;
+            }
             if (t > 0) {
                 iters = t;
                 est = rho;
@@ -578,8 +582,8 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
                 if (t >= max_iter) break;
                 prev_rho = rho;
             }
-            Lmax = (t == 0) ? 8 : levels_for(h_norm[2]);
-            if ((st = residual_update(R, As, Zs, e_row, f_col, dg, kp, np, Lmax, s))) break;
+            Lmax = levels_for(t == 0 ? 1.0 : h_norm[2], tol);
+            if ((st = residual_update(R, As, Zs, e_row, f_col, dg, Y, kp, np, Lmax, s))) break;
         }
         if (st) break;
         {
@@ -601,6 +605,16 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
 }
 
 }  // namespace gb
+
+extern "C" int gb_mixed_history(double *rho, int *levels, int cap)
+{
+    const int n = gb::tl_nhist < cap ? gb::tl_nhist : cap;
+    for (int i = 0; i < n; i++) {
+        if (rho) rho[i] = gb::tl_rho[i];
+        if (levels) levels[i] = gb::tl_levels[i];
+    }
+    return gb::tl_nhist;
+}
 
 extern "C" int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
                               const double *A, int64_t lda, double *B, int64_t ldb, double tol, int prec,

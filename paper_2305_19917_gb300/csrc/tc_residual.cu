@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ,
                    double *__restrict__ R, int64_t ldr, const int *__restrict__ e_row,
                    const int *__restrict__ f_col, const double *__restrict__ dg,
-                   const __nv_bfloat16 *__restrict__ Zg, int64_t zslice, int k_lo, int k_hi, int Lmax,
-                   int nMt, int nNt, int *status)
+                   const __nv_bfloat16 *__restrict__ Zg, int64_t zslice, float *__restrict__ Yout, int k_lo,
+                   int k_hi, int Lmax, int nMt, int nNt, int *status)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -202,7 +202,11 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     const int gj = j0 + half * 64 + c0 + c;
                     double sub = ldexp(static_cast<double>(T[c0 + c]), ei + fj[c]);
                     if (has_diag) sub += di * ldexp(double(zv[c]), fj[c] - 12);
-                    R[gi + int64_t(gj) * ldr] = rv[c] - sub;
+                    const double rn = rv[c] - sub;
+                    R[gi + int64_t(gj) * ldr] = rn;
+                    // the launch holding row i's diagonal is the last to touch
+                    // it: it also writes the FP32 copy for the next solve
+                    if (has_diag && Yout) Yout[gi + int64_t(gj) * ldr] = float(rn);
                 }
             }
         }
@@ -222,7 +226,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 // (2 x np x kp BF16: slice q holds column j of z_q at Zs + q*np*kp + j*kp).
 // kp, np multiples of 128; k_lo, k_hi multiples of 64; k_hi - k_lo <= 16384.
 int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
-                       const double *dg, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
+                       const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
                        cudaStream_t s)
 {
     if (kp <= 0 || np <= 0 || k_hi <= k_lo) return 0;
@@ -264,8 +268,8 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
     for (int p = 0; p < Lmax - 1; p++) flops += 2.0 * BM * tri * np * ((p + 3 <= Lmax) ? 2 : 1);
     LaunchScope ls(KK_RESIDUAL, s, flops, 16.0 * kp * np);
     tc_residual_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(
-        ta, tz, R, ldr, e_row, f_col, dg, static_cast<const __nv_bfloat16 *>(Zs), np * kp, (int)k_lo, (int)k_hi,
-        Lmax, (int)nM, (int)nN, st);
+        ta, tz, R, ldr, e_row, f_col, dg, static_cast<const __nv_bfloat16 *>(Zs), np * kp, Yout, (int)k_lo,
+        (int)k_hi, Lmax, (int)nM, (int)nN, st);
     return check(cudaGetLastError());
 }
 
