@@ -53,7 +53,9 @@ enum {
     GB_STATUS_NOT_CONVERGED = 1, /* refinement stopped before reaching tol  */
     GB_STATUS_CUDA_ERROR = 2,    /* a CUDA call failed; see gb_last_cuda_error */
     GB_STATUS_TIMEOUT = 3,       /* a device-side wait hit its iteration cap */
-    GB_STATUS_NO_MODEL = 4       /* no cost model loaded where one is needed */
+    GB_STATUS_NO_MODEL = 4,      /* no cost model loaded where one is needed */
+    GB_STATUS_SCRATCH_TOO_SMALL = 5 /* problem exceeds the fixed scratch of
+                                       gb_dtrsm_mixed_noalloc              */
 };
 
 /* Decomposition drivers (the paper's three computation models). */
@@ -140,6 +142,28 @@ int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
                    int64_t n, double alpha, const double *A, int64_t lda,
                    double *B, int64_t ldb, double tol, int prec, int max_iter,
                    int *iters_out, double *est_err_out, void *stream);
+
+/*
+ * gb_dtrsm_mixed_noalloc: gb_dtrsm_mixed for callers that cannot allocate
+ * device memory (the paper has no counterpart; this is an interface
+ * addition).  Same arguments, results and status codes as gb_dtrsm_mixed;
+ * it calls no allocator: its work space is a fixed 16 MiB array inside the
+ * library image (held on every GPU that loads the library until the process
+ * exits).  That bounds the problem: the padded sizes kp = 128*ceil(k/128),
+ * np = 128*ceil(ncols/128) (k = order of A, ncols = right-hand sides) must
+ * satisfy roughly 16 kp^2 + 26 kp np + 1050 kp + 12 np + 4 KB <= 16 MiB
+ * (e.g. k = ncols = 512); larger problems return GB_STATUS_SCRATCH_TOO_SMALL
+ * without touching the GPU.  The first call on a device performs a one-time
+ * set-up (it looks up the array's device address), so make it before any
+ * stream capture.  Calls share the array: calls that overlap on the GPU race
+ * and must be serialised by the caller.  Synchronous, like gb_dtrsm_mixed;
+ * a device wait that timed out returns GB_STATUS_TIMEOUT.
+ */
+int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag,
+                           int64_t m, int64_t n, double alpha,
+                           const double *A, int64_t lda, double *B,
+                           int64_t ldb, double tol, int prec, int max_iter,
+                           int *iters_out, double *est_err_out, void *stream);
 
 /*
  * gb_mixed_history: refinement history of the last gb_dtrsm_mixed call made

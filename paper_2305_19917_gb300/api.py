@@ -19,6 +19,7 @@ NOTRANS, TRANS = 0, 1
 NONUNIT, UNIT = 0, 1
 DRIVER_BLOCKED, DRIVER_RECURSIVE, DRIVER_ITERATIVE, DRIVER_AUTO = 0, 1, 2, -1
 STATUS_OK, STATUS_NOT_CONVERGED, STATUS_CUDA_ERROR, STATUS_TIMEOUT, STATUS_NO_MODEL = 0, 1, 2, 3, 4
+STATUS_SCRATCH_TOO_SMALL = 5
 
 LIB_PATH = _build.LIB
 
@@ -50,6 +51,8 @@ _SIGS = {
     "gb_version": ([], i32),
     "gb_dtrsm_mixed": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32,
                         ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
+    "gb_dtrsm_mixed_noalloc": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32,
+                                ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
     "gb_mixed_history": ([ctypes.POINTER(dbl), ctypes.POINTER(i32), i32], i32),
     "gb_bf16_gemm_update": ([i64, i64, i64, vp, i64, vp, i64, vp, i64, flt, vp], i32),
     "gb_device_status": ([i32], i32),
@@ -123,6 +126,15 @@ def gb_dtrsm_mixed(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, pr
     it, est = i32(), dbl()
     st = lib().gb_dtrsm_mixed(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
                               ctypes.byref(it), ctypes.byref(est), stream or None)
+    return st, it.value, est.value
+
+
+def gb_dtrsm_mixed_noalloc(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, stream=0):
+    """As gb_dtrsm_mixed, with the library's fixed scratch instead of any
+    device allocation.  Returns (status, iters, est_err)."""
+    it, est = i32(), dbl()
+    st = lib().gb_dtrsm_mixed_noalloc(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
+                                      ctypes.byref(it), ctypes.byref(est), stream or None)
     return st, it.value, est.value
 
 

@@ -155,6 +155,7 @@ const char *gb_status_string(int status)
     case GB_STATUS_CUDA_ERROR: return "CUDA error (see gb_last_cuda_error)";
     case GB_STATUS_TIMEOUT: return "device-side wait exceeded its iteration limit";
     case GB_STATUS_NO_MODEL: return "no cost model loaded";
+    case GB_STATUS_SCRATCH_TOO_SMALL: return "problem too large for the fixed no-allocation scratch";
     default: return "unknown status";
     }
 }

@@ -26,14 +26,15 @@
 #include <cuda_bf16.h>
 #include "common.cuh"
 #include "driver.cuh"
+#include "mixed.cuh"
 
 namespace gb {
 
 int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
-                        int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s);
+                        int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s, int *status);
 int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
                        const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
-                       cudaStream_t s);
+                       cudaStream_t s, int *status);
 int tc_gemm_prepare();
 int diag_inv_prepare();
 int launch_invert_blocks(const float *band, float *inv, int64_t nblocks, cudaStream_t s);
@@ -349,6 +350,7 @@ struct LowExec {
     const float *binv;  // inverses of the diagonal kBand-blocks
     int64_t kp, np;
     cudaStream_t s;
+    int *status_word;   // device word for wait timeouts (nullptr = library's own)
     int status = 0;
     bool ok() const { return status == 0; }
     void ts(int64_t b0, int64_t nr, float a)
@@ -364,7 +366,8 @@ struct LowExec {
     void gemm(int64_t ci0, int64_t M, int64_t ak0, int64_t K, float a)
     {
         if (status) return;
-        status = launch_tc_gemm_bf16(M, np, K, Abf + ci0 * kp + ak0, kp, Ybf + ak0, kp, Y + ci0, kp, a, s);
+        status = launch_tc_gemm_bf16(M, np, K, Abf + ci0 * kp + ak0, kp, Ybf + ak0, kp, Y + ci0, kp, a, s,
+                                     status_word);
     }
 };
 
@@ -392,11 +395,11 @@ int levels_for(double rho, double tol)
 }
 
 int residual_update(double *R, const __nv_bfloat16 *As, const __nv_bfloat16 *Zs, const int *e_row, const int *f_col,
-                    const double *dg, float *Y, int64_t kp, int64_t np, int Lmax, cudaStream_t s)
+                    const double *dg, float *Y, int64_t kp, int64_t np, int Lmax, cudaStream_t s, int *status_word)
 {
     for (int64_t lo = 0; lo < kp; lo += 16384) {
         int64_t hi = lo + 16384 < kp ? lo + 16384 : kp;
-        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, dg, Y, kp, np, lo, hi, Lmax, s));
+        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, dg, Y, kp, np, lo, hi, Lmax, s, status_word));
     }
     return 0;
 }
@@ -465,38 +468,55 @@ static thread_local double tl_rho[64];
 static thread_local int tl_levels[64];
 static thread_local int tl_nhist = 0;
 
-int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
-                     int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
-                     double *est_err_out, cudaStream_t s)
+MixedLayout mixed_layout(int side, int64_t m, int64_t n)
 {
+    MixedLayout L;
     const int64_t k = side == GB_LEFT ? m : n;
     const int64_t ncols = side == GB_LEFT ? n : m;
-    const bool mt = side == GB_LEFT ? (trans == GB_TRANS) : (trans == GB_NOTRANS);
-    const bool forward = (uplo == GB_LOWER) != mt;
-    const int64_t kp = (k + 127) / 128 * 128;
-    const int64_t np = (ncols + 127) / 128 * 128;
-    (void)prec;
-
-    View v{A, lda, mt, !forward, diag == GB_UNIT, k};
-    tl_nhist = 0;
-
-    // ---- workspace layout ----
-    const size_t kk = size_t(kp) * size_t(kp), kn = size_t(kp) * size_t(np);
+    L.kp = (k + 127) / 128 * 128;
+    L.np = (ncols + 127) / 128 * 128;
+    const size_t kk = size_t(L.kp) * size_t(L.kp), kn = size_t(L.kp) * size_t(L.np);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
         off += (bytes + 255) & ~size_t(255);
         return o;
     };
-    size_t o_abf = take(kk * 2), o_as = take(kk * 2 * kSlices), o_band = take(size_t(kp) * kBand * 4);
-    size_t o_binv = take(size_t(kp) * kBand * 4);
-    size_t o_r = take(kn * 8), o_x = take(kn * 8), o_y = take(kn * 4), o_ybf = take(kn * 2), o_zs = take(kn * 4);
-    size_t o_e = take(size_t(kp) * 4), o_f = take(size_t(np) * 4), o_norm = take(64), o_dg = take(size_t(kp) * 8);
-    size_t o_xm = take(size_t(np) * 4);
-    cudaMemPool_t pool = library_pool();
-    if (!pool) return GB_STATUS_CUDA_ERROR;
-    char *ws = nullptr;
-    GB_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&ws), off, pool, s));
+    L.o_abf = take(kk * 2);
+    L.o_as = take(kk * 2 * kSlices);
+    L.o_band = take(size_t(L.kp) * kBand * 4);
+    L.o_binv = take(size_t(L.kp) * kBand * 4);
+    L.o_r = take(kn * 8);
+    L.o_x = take(kn * 8);
+    L.o_y = take(kn * 4);
+    L.o_ybf = take(kn * 2);
+    L.o_zs = take(kn * 4);
+    L.o_e = take(size_t(L.kp) * 4);
+    L.o_f = take(size_t(L.np) * 4);
+    L.o_norm = take(64);
+    L.o_dg = take(size_t(L.kp) * 8);
+    L.o_xm = take(size_t(L.np) * 4);
+    L.total = off;
+    return L;
+}
+
+int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
+               int64_t lda, double *B, int64_t ldb, double tol, int max_iter, int *iters_out, double *est_err_out,
+               cudaStream_t s, char *ws, int *status_word, bool use_graph)
+{
+    const int64_t k = side == GB_LEFT ? m : n;
+    const int64_t ncols = side == GB_LEFT ? n : m;
+    const bool mt = side == GB_LEFT ? (trans == GB_TRANS) : (trans == GB_NOTRANS);
+    const bool forward = (uplo == GB_LOWER) != mt;
+    const MixedLayout L = mixed_layout(side, m, n);
+    const int64_t kp = L.kp, np = L.np;
+    const size_t kn = size_t(kp) * size_t(np);
+
+    View v{A, lda, mt, !forward, diag == GB_UNIT, k};
+    tl_nhist = 0;
+    const size_t o_abf = L.o_abf, o_as = L.o_as, o_band = L.o_band, o_binv = L.o_binv, o_r = L.o_r, o_x = L.o_x;
+    const size_t o_y = L.o_y, o_ybf = L.o_ybf, o_zs = L.o_zs, o_e = L.o_e, o_f = L.o_f, o_norm = L.o_norm;
+    const size_t o_dg = L.o_dg, o_xm = L.o_xm;
     auto *Abf = reinterpret_cast<__nv_bfloat16 *>(ws + o_abf);
     auto *As = reinterpret_cast<__nv_bfloat16 *>(ws + o_as);
     auto *band = reinterpret_cast<float *>(ws + o_band);
@@ -537,17 +557,20 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
             if ((st = check(cudaGetLastError()))) break;
         }
         if ((st = launch_invert_blocks(band, binv, kp / kBand, s))) break;
-        LowExec le{Y, Ybf, Abf, binv, kp, np, s};
+        LowExec le{Y, Ybf, Abf, binv, kp, np, s, status_word};
         LowGraph *lg = nullptr;
-        if ((st = low_graph(le, ws, &lg))) break;
+        if (use_graph && (st = low_graph(le, ws, &lg))) break;
         const int64_t nel = int64_t(kn);
         int Lmax = 8;
         double nx = 0, prev_rho = 0;
         for (int t = 0;; t++) {
             // Y = float(R) was written by prepB (t = 0) or by the residual kernel
-            {
+            if (use_graph) {
                 LaunchScope ls(KK_GRAPH, s, double(kp) * double(kp) * double(np), 0.0, lg->nkernels);
                 if ((st = check(cudaGraphLaunch(lg->exec, s)))) break;
+            } else {
+                le.status = 0;
+                if ((st = low_solve(le, kp))) break;
             }
             if ((st = check(cudaMemsetAsync(norms, 0, 3 * sizeof(double), s)))) break;
             {
@@ -583,7 +606,7 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
                 prev_rho = rho;
             }
             Lmax = levels_for(t == 0 ? 1.0 : h_norm[2], tol);
-            if ((st = residual_update(R, As, Zs, e_row, f_col, dg, Y, kp, np, Lmax, s))) break;
+            if ((st = residual_update(R, As, Zs, e_row, f_col, dg, Y, kp, np, Lmax, s, status_word))) break;
         }
         if (st) break;
         {
@@ -593,7 +616,6 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
             if ((st = check(cudaGetLastError()))) break;
         }
     } while (0);
-    cudaFreeAsync(ws, s);
     if (st == 0) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = check(e);
@@ -602,6 +624,23 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
     if (est_err_out) *est_err_out = est;
     if (st) return st;
     return (est <= tol) ? 0 : GB_STATUS_NOT_CONVERGED;
+}
+
+
+int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
+                     int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
+                     double *est_err_out, cudaStream_t s)
+{
+    (void)prec;
+    const MixedLayout L = mixed_layout(side, m, n);
+    cudaMemPool_t pool = library_pool();
+    if (!pool) return GB_STATUS_CUDA_ERROR;
+    char *ws = nullptr;
+    GB_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&ws), L.total, pool, s));
+    const int st = mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, max_iter, iters_out,
+                              est_err_out, s, ws, nullptr, true);
+    cudaFreeAsync(ws, s);
+    return st;
 }
 
 }  // namespace gb
@@ -616,12 +655,10 @@ extern "C" int gb_mixed_history(double *rho, int *levels, int cap)
     return gb::tl_nhist;
 }
 
-extern "C" int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
-                              const double *A, int64_t lda, double *B, int64_t ldb, double tol, int prec,
-                              int max_iter, int *iters_out, double *est_err_out, void *stream)
+namespace gb {
+int mixed_validate(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
+                   int64_t lda, const double *B, int64_t ldb, double tol, int prec, int max_iter)
 {
-    if (iters_out) *iters_out = 0;
-    if (est_err_out) *est_err_out = 0;
     if (side != GB_LEFT && side != GB_RIGHT) return -1;
     if (uplo != GB_LOWER && uplo != GB_UPPER) return -2;
     if (trans != GB_NOTRANS && trans != GB_TRANS) return -3;
@@ -637,14 +674,26 @@ extern "C" int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m
     if (!(tol >= 0.0)) return -12;
     if (prec != GB_PREC_BF16) return -13;
     if (max_iter < 1 || max_iter > 1000) return -14;
-    if (empty) return 0;
+    return 0;
+}
+}  // namespace gb
+
+extern "C" int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
+                              const double *A, int64_t lda, double *B, int64_t ldb, double tol, int prec,
+                              int max_iter, int *iters_out, double *est_err_out, void *stream)
+{
+    if (iters_out) *iters_out = 0;
+    if (est_err_out) *est_err_out = 0;
+    const int v = gb::mixed_validate(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter);
+    if (v) return v;
+    if (m == 0 || n == 0) return 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (alpha == 0.0) {
         gb::Canon<double> c{};
         c.B = B;
         c.ldb = ldb;
         c.left = side == GB_LEFT;
-        c.k = k;
+        c.k = side == GB_LEFT ? m : n;
         c.ncols = side == GB_LEFT ? n : m;
         c.stream = s;
         int st = gb::launch_zero(c);

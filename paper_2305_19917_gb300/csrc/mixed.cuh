@@ -1,0 +1,32 @@
+// Mixed-precision solve: work-space layout and core routine shared by the
+// allocating entry point and the no-allocation one (internal header).
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace gb {
+
+// Byte offsets of the work arrays of one mixed solve (k and the number of
+// right-hand sides padded to multiples of 128 as kp, np); `total` bytes.
+struct MixedLayout {
+    int64_t kp, np;
+    size_t o_abf, o_as, o_band, o_binv, o_r, o_x, o_y, o_ybf, o_zs, o_e, o_f, o_norm, o_dg, o_xm;
+    size_t total;
+};
+MixedLayout mixed_layout(int side, int64_t m, int64_t n);
+
+// The refinement solve on a caller-provided work space `ws` (layout above,
+// 256-byte aligned), with `status_word` as the device word for wait
+// timeouts (nullptr = the library's own) and the low-precision solve either
+// replayed from a cached CUDA graph (use_graph) or launched directly.
+// Arguments are assumed valid; alpha != 0; m, n > 0.  Synchronous.
+int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
+               int64_t lda, double *B, int64_t ldb, double tol, int max_iter, int *iters_out, double *est_err_out,
+               cudaStream_t s, char *ws, int *status_word, bool use_graph);
+
+// Argument checks of gb_dtrsm_mixed (0 or -i).
+int mixed_validate(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
+                   int64_t lda, const double *B, int64_t ldb, double tol, int prec, int max_iter);
+
+}  // namespace gb

@@ -223,7 +223,7 @@ int tc_gemm_prepare()
 
 template <int BN>
 static int launch_bn(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
-                     float *C, int64_t ldc, float alpha, cudaStream_t s)
+                     float *C, int64_t ldc, float alpha, cudaStream_t s, int *status)
 {
     CUtensorMap ta, tb;
     {
@@ -238,8 +238,9 @@ static int launch_bn(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda
         uint32_t box[2] = {BK, uint32_t(BN)};
         GB_TRY(encode_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, strides, box));
     }
-    GB_TRY(tc_gemm_prepare());
-    int *st = device_status_word();
+    GB_TRY(prepare_bn<BN>());
+    int *st = status ? status : device_status_word();
+    if (!st) return GB_STATUS_CUDA_ERROR;
     // 1-D grid (grouped rasterisation)
     const int64_t nM = (M + BM - 1) / BM, nN = (N + BN - 1) / BN;
     if (nM > 65535 || nN > 65535 || nM * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
@@ -252,11 +253,13 @@ static int launch_bn(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda
 
 // C (M x N, FP32, column-major, ldc) = alpha*C - A*B with A (M x K, BF16
 // row-major, lda) and B (K x N, BF16 column-major, ldb).  K % 64 == 0,
-// lda % 8 == 0, ldb % 8 == 0, A and B 16-byte aligned.  The N-tile width is
+// lda % 8 == 0, ldb % 8 == 0, A and B 16-byte aligned; `status` is the
+// device word that records wait timeouts (nullptr = the library's own word,
+// allocated on first use).  The N-tile width is
 // the widest of 256 / 128 / 64 that still gives at least two CTAs per SM
 // of work (small leaf updates use narrow tiles to spread over the GPU).
 int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
-                        int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s)
+                        int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s, int *status)
 {
     if (M <= 0 || N <= 0) return 0;
     if (K <= 0 || K % BK || lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) ||
@@ -264,9 +267,11 @@ int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t 
         return GB_STATUS_CUDA_ERROR;
     if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     const int64_t mt = (M + BM - 1) / BM;
-    if (mt * ((N + 255) / 256) >= 2 * 152) return launch_bn<256>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s);
-    if (mt * ((N + 127) / 128) >= 2 * 152) return launch_bn<128>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s);
-    return launch_bn<64>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s);
+    if (mt * ((N + 255) / 256) >= 2 * 152)
+        return launch_bn<256>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
+    if (mt * ((N + 127) / 128) >= 2 * 152)
+        return launch_bn<128>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
+    return launch_bn<64>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
 }
 
 }  // namespace gb
@@ -285,7 +290,8 @@ extern "C" int gb_bf16_gemm_update(int64_t M, int64_t N, int64_t K, const void *
     if (ldc < (M > 1 ? M : 1)) return -9;
     if (M == 0 || N == 0) return 0;
     if (K == 0) return 0;
-    return gb::launch_tc_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, alpha, static_cast<cudaStream_t>(stream));
+    return gb::launch_tc_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, alpha, static_cast<cudaStream_t>(stream),
+                                   nullptr);
 }
 
 extern "C" int gb_device_status(int clear)

@@ -227,7 +227,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 // kp, np multiples of 128; k_lo, k_hi multiples of 64; k_hi - k_lo <= 16384.
 int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
                        const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
-                       cudaStream_t s)
+                       cudaStream_t s, int *status)
 {
     if (kp <= 0 || np <= 0 || k_hi <= k_lo) return 0;
     if (kp % 128 || np % 128 || k_lo % 64 || k_hi % 64 || k_hi - k_lo > 16384 || Lmax < 2 || Lmax > 8)
@@ -252,7 +252,7 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
                                      (int)SMEM_BYTES));
         attr = true;
     }
-    int *st = device_status_word();
+    int *st = status ? status : device_status_word();
     if (!st) return GB_STATUS_CUDA_ERROR;
     // 1-D grid of nM*nN CTAs (grouped rasterisation)
     const int64_t nM = kp / BM, nN = np / BNO;
