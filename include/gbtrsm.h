@@ -175,6 +175,53 @@ int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag,
 int gb_mixed_history(double *rho, int *levels, int cap);
 
 /*
+ * Batched uneven solves (many independent problems of different order and
+ * width, each "n instances of TS" as in Section IV) in one persistent kernel
+ * launch driven by a device-side work queue, replayed from a CUDA graph.
+ *
+ * gb_trsm_batched(dtype, count, side[], uplo[], trans[], diag[], m[], n[],
+ *                 alpha[], A[], lda[], B[], ldb[], stream)
+ *   1 dtype   0 = FP64 (double), 1 = FP32 (float)
+ *   2 count   number of problems (>= 0)
+ *   3..13     HOST arrays of `count` entries: the gb_dtrsm arguments of
+ *             each problem; alpha[] holds doubles (dtype 0) or floats
+ *             (dtype 1); A[i] and B[i] are DEVICE pointers (column-major),
+ *             B[i] overwritten by X_i
+ *  14 stream
+ * A negative status -a names the argument a whose entry is invalid (or
+ * whose array is NULL).  Problems of order (m for Left, n for Right) up to
+ * 512 are solved in shared memory by the persistent kernel, in chunks of 16
+ * (FP64) or 32 (FP32) right-hand sides, largest first; larger problems are
+ * solved one after the other by the regular driver on the same stream.
+ * Synchronous (returns after the solves completed).
+ *
+ * gb_batched_plan_create(... same 1-14 ..., void **plan_out) builds the work
+ * queue once (device descriptor array, CUDA graph) for the given pointers;
+ * gb_batched_plan_run(plan, stream) replays it (asynchronous; the pointed-to
+ * data may change between runs, the pointers and sizes may not);
+ * gb_batched_plan_destroy(plan) frees it; gb_batched_plan_info reports the
+ * number of work units, the persistent grid size, the number of problems
+ * handled by the regular driver and the algorithmic flops (sum of k^2 ncols).
+ */
+int gb_trsm_batched(int dtype, int64_t count, const int8_t *side,
+                    const int8_t *uplo, const int8_t *trans,
+                    const int8_t *diag, const int64_t *m, const int64_t *n,
+                    const void *alpha, const void *const *A,
+                    const int64_t *lda, void *const *B, const int64_t *ldb,
+                    void *stream);
+int gb_batched_plan_create(int dtype, int64_t count, const int8_t *side,
+                           const int8_t *uplo, const int8_t *trans,
+                           const int8_t *diag, const int64_t *m,
+                           const int64_t *n, const void *alpha,
+                           const void *const *A, const int64_t *lda,
+                           void *const *B, const int64_t *ldb, void *stream,
+                           void **plan_out);
+int gb_batched_plan_run(void *plan, void *stream);
+int gb_batched_plan_destroy(void *plan);
+int gb_batched_plan_info(const void *plan, int64_t *units, int *grid,
+                         int64_t *large_instances, double *flops);
+
+/*
  * gb_plan_counts: host-only description of the launches a plan issues for a
  * triangle of order k (no GPU work).  Writes the number of diagonal-block
  * solves and of GEMM updates, and the sum over GEMMs of M*N*K / ncols (i.e.

@@ -53,6 +53,13 @@ _SIGS = {
                         ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
     "gb_dtrsm_mixed_noalloc": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32,
                                 ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
+    "gb_trsm_batched": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
+    "gb_batched_plan_create": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                ctypes.POINTER(vp)], i32),
+    "gb_batched_plan_run": ([vp, vp], i32),
+    "gb_batched_plan_destroy": ([vp], i32),
+    "gb_batched_plan_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
+                              ctypes.POINTER(dbl)], i32),
     "gb_mixed_history": ([ctypes.POINTER(dbl), ctypes.POINTER(i32), i32], i32),
     "gb_bf16_gemm_update": ([i64, i64, i64, vp, i64, vp, i64, vp, i64, flt, vp], i32),
     "gb_device_status": ([i32], i32),
@@ -136,6 +143,73 @@ def gb_dtrsm_mixed_noalloc(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb,
     st = lib().gb_dtrsm_mixed_noalloc(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
                                       ctypes.byref(it), ctypes.byref(est), stream or None)
     return st, it.value, est.value
+
+
+class _BatchArgs:
+    """Host descriptor arrays of a batch (kept alive while in use)."""
+
+    def __init__(self, dtype, items):
+        import numpy as np
+        c = len(items)
+        self.count = c
+        self.side = np.array([it["side"] for it in items], dtype=np.int8)
+        self.uplo = np.array([it["uplo"] for it in items], dtype=np.int8)
+        self.trans = np.array([it["trans"] for it in items], dtype=np.int8)
+        self.diag = np.array([it["diag"] for it in items], dtype=np.int8)
+        self.m = np.array([it["m"] for it in items], dtype=np.int64)
+        self.n = np.array([it["n"] for it in items], dtype=np.int64)
+        self.alpha = np.array([it["alpha"] for it in items], dtype=np.float64 if dtype == 0 else np.float32)
+        self.A = (ctypes.c_void_p * max(c, 1))(*[it["A_ptr"] for it in items])
+        self.B = (ctypes.c_void_p * max(c, 1))(*[it["B_ptr"] for it in items])
+        self.lda = np.array([it["lda"] for it in items], dtype=np.int64)
+        self.ldb = np.array([it["ldb"] for it in items], dtype=np.int64)
+
+    def args(self):
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        return [self.count, p(self.side), p(self.uplo), p(self.trans), p(self.diag), p(self.m), p(self.n),
+                p(self.alpha), ctypes.cast(self.A, ctypes.c_void_p), p(self.lda),
+                ctypes.cast(self.B, ctypes.c_void_p), p(self.ldb)]
+
+
+def gb_trsm_batched(dtype, items, stream=0):
+    """items: list of dicts with side, uplo, trans, diag, m, n, alpha, A_ptr,
+    lda, B_ptr, ldb (device pointers as ints).  Returns the status."""
+    a = _BatchArgs(dtype, items)
+    return lib().gb_trsm_batched(dtype, *a.args(), stream or None)
+
+
+class BatchedPlan:
+    """gb_batched_plan_* handle (work queue + CUDA graph for fixed pointers)."""
+
+    def __init__(self, dtype, items, stream=0):
+        self._args = _BatchArgs(dtype, items)
+        h = vp()
+        st = lib().gb_batched_plan_create(dtype, *self._args.args(), stream or None, ctypes.byref(h))
+        if st != 0:
+            raise GbError("gb_batched_plan_create", st)
+        self.handle = h
+
+    def run(self, stream=0):
+        st = lib().gb_batched_plan_run(self.handle, stream or None)
+        if st != 0:
+            raise GbError("gb_batched_plan_run", st)
+
+    def info(self):
+        u, g, big, fl = i64(), i32(), i64(), dbl()
+        lib().gb_batched_plan_info(self.handle, ctypes.byref(u), ctypes.byref(g), ctypes.byref(big),
+                                   ctypes.byref(fl))
+        return dict(units=u.value, grid=g.value, large_instances=big.value, flops=fl.value)
+
+    def close(self):
+        if self.handle:
+            lib().gb_batched_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gb_mixed_history(cap=64):

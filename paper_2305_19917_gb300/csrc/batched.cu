@@ -1,0 +1,438 @@
+// Batched uneven triangular solves in one persistent launch: "n instances of
+// TS" (Section IV, many right-hand sides) generalised to many independent
+// problems of different order and width.
+//
+// Work units are (instance, chunk of CW right-hand sides); a chunk of an
+// order-k instance costs ~k^2 CW / 2 multiply-adds, so units are sorted by
+// k (largest first) and handed out through a device-side work queue: each
+// CTA of a persistent grid pops a ticket with one atomicAdd until the queue
+// is empty (no CTA ever waits on another).  A unit is solved entirely in
+// shared memory by its CTA with the blocked forward model of Section V-C in
+// left-looking order: for each 32-row diagonal block, one register-tiled
+// update with all solved blocks (the gemm tasks), then the 32 x 32 triangle
+// by warp-shuffle substitution (the TS task).  Backward problems are index
+// reversed and right-side problems transposed on the way in and out.
+// Instances of order above KMAX are solved by the regular driver.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+#include "common.cuh"
+
+namespace gb {
+
+namespace {
+
+constexpr int KMAX = 512;   // largest order solved in shared memory
+constexpr int NBB = 32;     // diagonal block
+constexpr int NT = 256;     // threads per CTA
+
+template <typename T>
+struct BCfg;
+template <>
+struct BCfg<double> {
+    static constexpr int CW = 16;  // right-hand sides per unit
+};
+template <>
+struct BCfg<float> {
+    static constexpr int CW = 32;
+};
+
+template <typename T>
+struct Unit {
+    const T *A;   // A of the instance
+    T *B;         // B of the instance, offset to the chunk's first right-hand side
+    int64_t lda, ldb;
+    int k;        // order of the triangle
+    int cw;       // right-hand sides in this chunk (<= CW)
+    int flags;    // bit0 mt, bit1 rev (backward), bit2 unit diag, bit3 left
+    T alpha;
+};
+
+template <typename T>
+__device__ __forceinline__ T mv_rev(const Unit<T> &u, int i, int j)
+{
+    const bool mt = u.flags & 1, rev = u.flags & 2;
+    const int io = rev ? u.k - 1 - i : i, jo = rev ? u.k - 1 - j : j;
+    return mt ? u.A[jo + int64_t(io) * u.lda] : u.A[io + int64_t(jo) * u.lda];
+}
+
+// smem: Xs[KMAX][CW+1], tile Ts[NBB][NBB+1], inverse diagonal.
+template <typename T>
+__global__ void __launch_bounds__(NT)
+batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restrict__ ticket)
+{
+    constexpr int CW = BCfg<T>::CW;
+    constexpr int LX = CW + 1;
+    constexpr int PER = CW / 8;  // outputs per thread in the update (8 threads per row)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);
+    T *Ts = Xs + KMAX * LX;
+    T *inv = Ts + NBB * (NBB + 1);
+    __shared__ int cur;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (;;) {
+        if (tid == 0) cur = int(atomicAdd(ticket, 1u));
+        __syncthreads();
+        const int t = cur;
+        __syncthreads();
+        if (t >= nunits) return;
+        const Unit<T> u = units[t];
+        const int k = u.k, cw = u.cw;
+        const bool mt = u.flags & 1, rev = u.flags & 2, unitd = u.flags & 4, left = u.flags & 8;
+
+        // ---- Xs = alpha * Bv' (forward view of the chunk) ------------------
+        for (int idx = tid; idx < k * CW; idx += NT) {
+            int i, c;
+            if (left) { i = idx % k; c = idx / k; }   // contiguous along i
+            else      { c = idx % CW; i = idx / CW; }  // contiguous along c
+            T v = T(0);
+            if (c < cw) {
+                const int io = rev ? k - 1 - i : i;
+                v = u.alpha * (left ? u.B[io + int64_t(c) * u.ldb] : u.B[c + int64_t(io) * u.ldb]);
+            }
+            Xs[i * LX + c] = v;
+        }
+        __syncthreads();
+
+        const int nblk = (k + NBB - 1) / NBB;
+        for (int jb = 0; jb < nblk; jb++) {
+            const int j0 = jb * NBB;
+            const int nr = min(NBB, k - j0);
+            // ---- gemm tasks: X_j -= Mv'(j, i) X_i for all solved blocks i ---
+            const int r = tid >> 3, cq = (tid & 7) * PER;
+            T acc[PER];
+#pragma unroll
+            for (int e = 0; e < PER; e++) acc[e] = T(0);
+            for (int ib = 0; ib < jb; ib++) {
+                const int i0 = ib * NBB;
+                for (int idx = tid; idx < NBB * NBB; idx += NT) {
+                    const int fast = idx % NBB, slow = idx / NBB;
+                    // read along A's contiguous dimension
+                    int rr, kk;
+                    if (!mt) { rr = fast; kk = slow; }
+                    else     { kk = fast; rr = slow; }
+                    T v = T(0);
+                    if (rr < nr) v = mv_rev(u, j0 + rr, i0 + kk);
+                    Ts[rr * (NBB + 1) + kk] = v;
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int kk = 0; kk < NBB; kk++) {
+                    const T a = Ts[r * (NBB + 1) + kk];
+#pragma unroll
+                    for (int e = 0; e < PER; e++) acc[e] += a * Xs[(i0 + kk) * LX + cq + e];
+                }
+                __syncthreads();
+            }
+            if (r < nr) {
+#pragma unroll
+                for (int e = 0; e < PER; e++) Xs[(j0 + r) * LX + cq + e] -= acc[e];
+            }
+            // ---- TS task: the nr x nr triangle by warp-shuffle substitution -
+            for (int idx = tid; idx < NBB * NBB; idx += NT) {
+                const int fast = idx % NBB, slow = idx / NBB;
+                int rr, kk;
+                if (!mt) { rr = fast; kk = slow; }
+                else     { kk = fast; rr = slow; }
+                T v = T(0);
+                if (rr < nr && kk < nr && kk < rr) v = mv_rev(u, j0 + rr, j0 + kk);
+                Ts[rr * (NBB + 1) + kk] = v;
+            }
+            if (tid < NBB) inv[tid] = (tid < nr && !unitd) ? T(1) / mv_rev(u, j0 + tid, j0 + tid) : T(1);
+            __syncthreads();
+            // warp w solves columns w, w+8, ... (PER columns, interleaved for ILP)
+            {
+                T tv[PER];
+#pragma unroll
+                for (int e = 0; e < PER; e++) tv[e] = (lane < nr) ? Xs[(j0 + lane) * LX + warp + 8 * e] : T(0);
+                for (int kk = 0; kk < nr; kk++) {
+                    const T d = inv[kk];
+                    const T lk = Ts[lane * (NBB + 1) + kk];
+#pragma unroll
+                    for (int e = 0; e < PER; e++) {
+                        const T x = __shfl_sync(0xffffffffu, tv[e], kk) * d;
+                        if (lane == kk) tv[e] = x;
+                        else if (lane > kk) tv[e] -= lk * x;
+                    }
+                }
+                if (lane < nr) {
+#pragma unroll
+                    for (int e = 0; e < PER; e++) Xs[(j0 + lane) * LX + warp + 8 * e] = tv[e];
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- write back (undo reversal / transposition) ---------------------
+        for (int idx = tid; idx < k * CW; idx += NT) {
+            int i, c;
+            if (left) { i = idx % k; c = idx / k; }
+            else      { c = idx % CW; i = idx / CW; }
+            if (c < cw) {
+                const int io = rev ? k - 1 - i : i;
+                const T v = Xs[i * LX + c];
+                if (left) u.B[io + int64_t(c) * u.ldb] = v;
+                else u.B[c + int64_t(io) * u.ldb] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+constexpr size_t batched_smem()
+{
+    return sizeof(T) * (size_t(KMAX) * (BCfg<T>::CW + 1) + NBB * (NBB + 1) + NBB);
+}
+
+}  // namespace
+
+// ---- plan object ------------------------------------------------------------
+
+struct BatchedPlan {
+    int dtype = 0;                 // 0 FP64, 1 FP32
+    int64_t nunits = 0;
+    void *units = nullptr;         // device array of Unit<T>
+    unsigned *ticket = nullptr;    // device work-queue counter
+    int grid = 0;
+    // instances too large for shared memory, solved by the regular driver
+    struct Big {
+        int side, uplo, trans, diag;
+        int64_t m, n, lda, ldb;
+        double alpha;
+        const void *A;
+        void *B;
+    };
+    std::vector<Big> big;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t graph_kernels = 0;
+    double flops = 0, bytes = 0;
+};
+
+namespace {
+
+template <typename T>
+void build_units(BatchedPlan &P, int64_t count, const int8_t *side, const int8_t *uplo, const int8_t *trans,
+                 const int8_t *diag, const int64_t *m, const int64_t *n, const T *alpha, const void *const *A,
+                 const int64_t *lda, void *const *B, const int64_t *ldb, std::vector<Unit<T>> &units)
+{
+    constexpr int CW = BCfg<T>::CW;
+    for (int64_t i = 0; i < count; i++) {
+        if (m[i] == 0 || n[i] == 0) continue;
+        const bool left = side[i] == GB_LEFT;
+        const int64_t k = left ? m[i] : n[i];
+        const int64_t ncols = left ? n[i] : m[i];
+        P.flops += double(k) * double(k) * double(ncols);
+        P.bytes += sizeof(T) * (double(k) * double(k) / 2 + 2.0 * double(k) * double(ncols));
+        if (k > KMAX || alpha[i] == T(0)) {
+            P.big.push_back({side[i], uplo[i], trans[i], diag[i], m[i], n[i], lda[i], ldb[i], double(alpha[i]), A[i],
+                             B[i]});
+            continue;
+        }
+        const bool mt = left ? (trans[i] == GB_TRANS) : (trans[i] == GB_NOTRANS);
+        const bool fwd = (uplo[i] == GB_LOWER) != mt;
+        const int flags = (mt ? 1 : 0) | (fwd ? 0 : 2) | (diag[i] == GB_UNIT ? 4 : 0) | (left ? 8 : 0);
+        for (int64_t c0 = 0; c0 < ncols; c0 += CW) {
+            Unit<T> u;
+            u.A = static_cast<const T *>(A[i]);
+            T *b = static_cast<T *>(B[i]);
+            u.B = left ? b + c0 * ldb[i] : b + c0;
+            u.lda = lda[i];
+            u.ldb = ldb[i];
+            u.k = int(k);
+            u.cw = int(std::min<int64_t>(CW, ncols - c0));
+            u.flags = flags;
+            u.alpha = alpha[i];
+            units.push_back(u);
+        }
+    }
+    // largest first (longest-processing-time order for the work queue)
+    std::stable_sort(units.begin(), units.end(),
+                     [](const Unit<T> &a, const Unit<T> &b) { return a.k * a.cw > b.k * b.cw; });
+}
+
+template <typename T>
+int upload_and_capture(BatchedPlan &P, std::vector<Unit<T>> &units, cudaStream_t s)
+{
+    P.nunits = int64_t(units.size());
+    const size_t ub = units.size() * sizeof(Unit<T>);
+    GB_CUDA(cudaMalloc(&P.units, ub > 0 ? ub : sizeof(Unit<T>)));
+    GB_CUDA(cudaMalloc(&P.ticket, sizeof(unsigned)));
+    if (ub) GB_CUDA(cudaMemcpyAsync(P.units, units.data(), ub, cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    static bool attr = false;
+    if (!attr) {
+        GB_CUDA(cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)batched_smem<T>()));
+        attr = true;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T>, NT, batched_smem<T>()));
+    if (per_sm < 1) per_sm = 1;
+    int64_t g = int64_t(sms) * per_sm;
+    if (g > P.nunits) g = P.nunits;
+    P.grid = int(g);
+    if (P.nunits == 0) return 0;
+    // CUDA graph: [reset the queue counter, persistent kernel]
+    cudaStream_t cs;
+    GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const uint64_t before = capture_count();
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(P.ticket, 0, sizeof(unsigned), cs);
+        {
+            LaunchScope ls(KK_BATCHED, cs, P.flops, P.bytes);
+            batched_kernel<T><<<P.grid, NT, batched_smem<T>(), cs>>>(static_cast<const Unit<T> *>(P.units),
+                                                                     int(P.nunits), P.ticket);
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&P.exec, graph, 0);
+            cudaGraphDestroy(graph);
+        }
+    }
+    P.graph_kernels = capture_count() - before;
+    cudaStreamDestroy(cs);
+    return check(e);
+}
+
+}  // namespace
+
+int batched_run(BatchedPlan &P, cudaStream_t s)
+{
+    if (P.nunits > 0) {
+        LaunchScope ls(KK_BATCHED, s, P.flops, P.bytes, P.graph_kernels);
+        GB_CUDA(cudaGraphLaunch(P.exec, s));
+    }
+    for (auto &b : P.big) {
+        int st;
+        if (P.dtype == 0)
+            st = gb_dtrsm(b.side, b.uplo, b.trans, b.diag, b.m, b.n, b.alpha, static_cast<const double *>(b.A), b.lda,
+                          static_cast<double *>(b.B), b.ldb, s);
+        else
+            st = gb_strsm(b.side, b.uplo, b.trans, b.diag, b.m, b.n, float(b.alpha), static_cast<const float *>(b.A),
+                          b.lda, static_cast<float *>(b.B), b.ldb, s);
+        if (st) return st;
+    }
+    return 0;
+}
+
+void batched_free(BatchedPlan *P)
+{
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->units) cudaFree(P->units);
+    if (P->ticket) cudaFree(P->ticket);
+    delete P;
+}
+
+int batched_create(int dtype, int64_t count, const int8_t *side, const int8_t *uplo, const int8_t *trans,
+                   const int8_t *diag, const int64_t *m, const int64_t *n, const void *alpha, const void *const *A,
+                   const int64_t *lda, void *const *B, const int64_t *ldb, cudaStream_t s, BatchedPlan **out)
+{
+    // argument checks (1-based argument numbers of gb_trsm_batched)
+    if (dtype != 0 && dtype != 1) return -1;
+    if (count < 0) return -2;
+    if (count > 0) {
+        const void *arrays[11] = {side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb};
+        for (int a = 0; a < 11; a++)
+            if (!arrays[a]) return -(3 + a);
+    }
+    for (int64_t i = 0; i < count; i++) {
+        if (side[i] != GB_LEFT && side[i] != GB_RIGHT) return -3;
+        if (uplo[i] != GB_LOWER && uplo[i] != GB_UPPER) return -4;
+        if (trans[i] != GB_NOTRANS && trans[i] != GB_TRANS) return -5;
+        if (diag[i] != GB_NONUNIT && diag[i] != GB_UNIT) return -6;
+        if (m[i] < 0) return -7;
+        if (n[i] < 0) return -8;
+        const int64_t k = side[i] == GB_LEFT ? m[i] : n[i];
+        const bool empty = m[i] == 0 || n[i] == 0;
+        const double a = dtype == 0 ? static_cast<const double *>(alpha)[i] : static_cast<const float *>(alpha)[i];
+        if (!empty && A[i] == nullptr && a != 0.0) return -10;
+        if (lda[i] < (k > 1 ? k : 1)) return -11;
+        if (!empty && B[i] == nullptr) return -12;
+        if (ldb[i] < (m[i] > 1 ? m[i] : 1)) return -13;
+    }
+    BatchedPlan *P = new BatchedPlan;
+    P->dtype = dtype;
+    int st;
+    if (dtype == 0) {
+        std::vector<Unit<double>> units;
+        build_units<double>(*P, count, side, uplo, trans, diag, m, n, static_cast<const double *>(alpha), A, lda, B,
+                            ldb, units);
+        st = upload_and_capture<double>(*P, units, s);
+    } else {
+        std::vector<Unit<float>> units;
+        build_units<float>(*P, count, side, uplo, trans, diag, m, n, static_cast<const float *>(alpha), A, lda, B,
+                           ldb, units);
+        st = upload_and_capture<float>(*P, units, s);
+    }
+    if (st) {
+        batched_free(P);
+        return st;
+    }
+    *out = P;
+    return 0;
+}
+
+}  // namespace gb
+
+extern "C" {
+
+int gb_batched_plan_create(int dtype, int64_t count, const int8_t *side, const int8_t *uplo, const int8_t *trans,
+                           const int8_t *diag, const int64_t *m, const int64_t *n, const void *alpha,
+                           const void *const *A, const int64_t *lda, void *const *B, const int64_t *ldb,
+                           void *stream, void **plan_out)
+{
+    if (!plan_out) return -15;
+    *plan_out = nullptr;
+    gb::BatchedPlan *P = nullptr;
+    int st = gb::batched_create(dtype, count, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb,
+                                static_cast<cudaStream_t>(stream), &P);
+    if (st) return st;
+    *plan_out = P;
+    return 0;
+}
+
+int gb_batched_plan_run(void *plan, void *stream)
+{
+    if (!plan) return -1;
+    return gb::batched_run(*static_cast<gb::BatchedPlan *>(plan), static_cast<cudaStream_t>(stream));
+}
+
+int gb_batched_plan_destroy(void *plan)
+{
+    gb::batched_free(static_cast<gb::BatchedPlan *>(plan));
+    return 0;
+}
+
+int gb_batched_plan_info(const void *plan, int64_t *units, int *grid, int64_t *large_instances, double *flops)
+{
+    if (!plan) return -1;
+    const gb::BatchedPlan *P = static_cast<const gb::BatchedPlan *>(plan);
+    if (units) *units = P->nunits;
+    if (grid) *grid = P->grid;
+    if (large_instances) *large_instances = int64_t(P->big.size());
+    if (flops) *flops = P->flops;
+    return 0;
+}
+
+int gb_trsm_batched(int dtype, int64_t count, const int8_t *side, const int8_t *uplo, const int8_t *trans,
+                    const int8_t *diag, const int64_t *m, const int64_t *n, const void *alpha, const void *const *A,
+                    const int64_t *lda, void *const *B, const int64_t *ldb, void *stream)
+{
+    void *plan = nullptr;
+    int st = gb_batched_plan_create(dtype, count, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream, &plan);
+    if (st) return st;
+    st = gb_batched_plan_run(plan, stream);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    gb_batched_plan_destroy(plan);
+    if (st) return st;
+    return gb::check(e);
+}
+
+}  // extern "C"

@@ -156,3 +156,14 @@ def test_every_schedule_covers_the_triangle_once(lib):
 def test_stop_rule_is_strict():
     assert models.refine_further(10.0, 4.9)
     assert not models.refine_further(10.0, 5.0)
+
+
+def test_batched_argument_errors(lib):
+    from paper_2305_19917_gb300 import api
+    base = dict(side=0, uplo=0, trans=0, diag=0, m=4, n=3, alpha=1.0, A_ptr=0x1000, lda=4, B_ptr=0x2000, ldb=4)
+    for key, bad, code in [("side", 2, -3), ("uplo", 5, -4), ("trans", -1, -5), ("diag", 3, -6), ("m", -1, -7),
+                           ("n", -2, -8), ("A_ptr", 0, -10), ("lda", 3, -11), ("B_ptr", 0, -12), ("ldb", 2, -13)]:
+        d = dict(base)
+        d[key] = bad
+        assert api.gb_trsm_batched(0, [dict(base), d]) == code, key
+    assert api.gb_trsm_batched(7, [base]) == -1
