@@ -52,7 +52,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--m", type=int, default=16384)
     p.add_argument("--n", type=int, default=16384)
-    p.add_argument("--path", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--path", default="mixed", choices=["mixed", "fp64", "batched"])
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="batched path precision")
+    p.add_argument("--count", type=int, default=4096, help="batched path: number of problems")
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cols", type=int, default=0,
@@ -389,10 +391,147 @@ def run_ours(args):
     return 0
 
 
+# FP32 ALU peak for the batched FP32 roofline: 152 SMs x 128 FFMA/clk x 2
+# flop x 2.07 GHz (an FFMA probe measured 69.8 TFLOP/s).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_batched(args):
+    """The uneven batch: `count` problems, m log-uniform in [16, 512], n in
+    [1, 256], side/uplo uniform (seeded), one plan (work queue + CUDA graph)
+    replayed per step; all A in one device pool, all B in another, so the
+    per-step reset of B is a single copy outside the timed events."""
+    import torch
+
+    from paper_2305_19917_gb300 import api, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local if world > 1 else 0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    api.lib()
+    dt = 0 if args.dtype == "f64" else 1
+    tdt = torch.float64 if dt == 0 else torch.float32
+    items = inputs.make_batch(args.count, seed=0)
+    a_sizes = [it["A"].size for it in items]
+    b_sizes = [it["B"].size for it in items]
+    Apool = torch.empty(int(sum(a_sizes)) + 16, dtype=tdt, device="cuda")
+    Bpool = torch.empty(int(sum(b_sizes)) + 16, dtype=tdt, device="cuda")
+    descs, oa, ob = [], 0, 0
+    for it, sa, sb in zip(items, a_sizes, b_sizes):
+        m, n = it["B"].shape
+        k = it["A"].shape[0]
+        Apool[oa:oa + sa].copy_(torch.as_tensor(np.asfortranarray(it["A"]).ravel(order="F")).to(tdt))
+        Bpool[ob:ob + sb].copy_(torch.as_tensor(np.asfortranarray(it["B"]).ravel(order="F")).to(tdt))
+        descs.append(dict(side=it["side"], uplo=it["uplo"], trans=it["trans"], diag=it["diag"], m=m, n=n,
+                          alpha=it["alpha"], A_ptr=Apool.data_ptr() + oa * Apool.element_size(), lda=k,
+                          B_ptr=Bpool.data_ptr() + ob * Bpool.element_size(), ldb=m))
+        oa += sa
+        ob += sb
+    B0 = Bpool.clone()
+    stream = torch.cuda.current_stream()
+    plan = api.BatchedPlan(dt, descs, stream.cuda_stream)
+    info = plan.info()
+    flops = info["flops"]
+    esz = Apool.element_size()
+    alg_bytes = esz * sum(0.5 * it["A"].shape[0] ** 2 + 2 * it["B"].size for it in items)
+
+    def reset():
+        Bpool.copy_(B0)
+
+    def solve():
+        plan.run(stream.cuda_stream)
+
+    for _ in range(max(3, args.warmup)):
+        reset()
+        solve()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    api.gb_profile_enable(1)
+    l0 = api.gb_kernel_launches()
+    ms, _ = _timed_steps(solve, reset, args.steps, stream)
+    launches = api.gb_kernel_launches() - l0
+    clk = clocks.stop()
+    prof = api.gb_profile_read(api.KERNEL_KINDS.index("batched"))
+    api.gb_profile_enable(0)
+    ms_step = float(np.mean(ms))
+    if world > 1:
+        from paper_2305_19917_gb300 import dist as gdist
+        ms_step = gdist.max_over_ranks(ms_step, device="cuda")
+    value = world * flops / (ms_step * 1e-3) / 1e12
+    # accuracy on sampled instances
+    import oracle
+    errs = []
+    for idx in range(0, len(items), max(1, len(items) // 32)):
+        it = items[idx]
+        off = int(sum(b_sizes[:idx]))
+        X = Bpool[off:off + b_sizes[idx]].double().cpu().numpy().reshape(it["B"].shape, order="F")
+        Xo = oracle.dtrsm(it["side"], it["uplo"], it["trans"], it["diag"], it["alpha"], it["A"], it["B"])
+        errs.append(float(np.linalg.norm(X - Xo) / max(np.linalg.norm(Xo), 1e-300)))
+    # e2e: host pools in pinned memory, copied in and X copied out each step
+    A_pin = Apool.cpu().pin_memory()
+    B_pin = B0.cpu().pin_memory()
+    X_pin = torch.empty_like(B_pin).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    Apool.copy_(A_pin, non_blocking=True)
+    Bpool.copy_(B_pin, non_blocking=True)
+    solve()
+    X_pin.copy_(Bpool, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    peak = FP64_PEAK_TFLOPS if dt == 0 else FP32_PEAK_TFLOPS
+    achieved = prof["flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] > 0 else 0.0
+    hbm = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else 0.0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        t0 = time.perf_counter()
+        sample = items[: max(1, len(items) // 16)]
+        fl = 0.0
+        for it in sample:
+            oracle.dtrsm(it["side"], it["uplo"], it["trans"], it["diag"], it["alpha"], it["A"], it["B"])
+            k = it["A"].shape[0]
+            fl += float(k) * k * (it["B"].size // k)
+        dtc = time.perf_counter() - t0
+        cpu = {"value": fl / dtc / 1e12, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"first {len(sample)} of the {len(items)} problems, FP64 oracle, {dtc:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": f"batched uneven TRSM: {len(items)} problems, m log-uniform [16,512], "
+                                       f"n uniform [1,256], side/uplo uniform, seed 0; one persistent launch "
+                                       f"(device work queue, CUDA graph)",
+                           "units": info["units"], "grid": info["grid"],
+                           "l2": "B reset by one copy before each step; A+B pools exceed L2 "
+                                 f"({(Apool.numel() + Bpool.numel()) * esz / 1e6:.0f} MB)"},
+                "roofline": {"kernel": "batched", "bound": "alu", "achieved": achieved, "peak": peak,
+                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                             "peak_source": "derived from SM count x FMA units x 2.07 GHz",
+                             "hbm_gbs": hbm, "hbm_frac": hbm / MEASURED_PEAKS.get("hbm_gbs", 6797.2),
+                             "launches": prof["launches"], "ms_total": prof["ms"]},
+                "cpu_baseline": cpu,
+                "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+                        "h2d_bytes_per_step": int((Apool.numel() + Bpool.numel()) * esz),
+                        "d2h_bytes_per_step": int(Bpool.numel() * esz)},
+                "gpu_launches": int(launches), "clocks": clk,
+                "accuracy": {"fwd_err_max_sampled": max(errs), "instances_checked": len(errs)}}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.path == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 
