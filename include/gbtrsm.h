@@ -222,6 +222,76 @@ int gb_batched_plan_info(const void *plan, int64_t *units, int *grid,
                          int64_t *large_instances, double *flops);
 
 /*
+ * Planner, autotuner and cost model (the paper's analytical performance
+ * models of Section V -- Comp(i) and the refinement stop rule -- replaced by
+ * timings measured on the GPU and a network trained on them).
+ *
+ * gb_plan_candidates(dtype, out, cap): the standard candidate set (blocked
+ *   and iterative with nb in {16..512}, recursive with nb in {16..512} and
+ *   depth 1..6); writes up to cap plans, returns the set size (48).
+ * gb_plan_features(dtype, side, uplo, trans, m, n, plan, features): the
+ *   17 network inputs of (shape, plan): log2 m / 16, log2 n / 16, one-hots of
+ *   side, uplo, trans and dtype (0 FP64, 1 FP32, 2 BF16-mixed, 3 FP8-mixed),
+ *   log2 nb / 9, depth / 6, one-hot driver.  Returns 17.  Host only.
+ * gb_plan_set_model(path): load a trained network ("GBMLP001" file: magic,
+ *   int32 in_dim = 17, int32 hidden = 64, int32 parameter count, float mean
+ *   and scale of the log-time target, then the parameters); NULL unloads.
+ *   Returns 0 or -1 (unreadable / malformed).  While loaded, the planner of
+ *   gb_dtrsm / gb_strsm picks the predicted-fastest candidate; the first
+ *   call for a new shape runs one inference launch and waits for it.
+ * gb_plan_choose(dtype, side, uplo, trans, m, n, plan_out, predicted_ms):
+ *   the model's choice (GB_STATUS_NO_MODEL and the built-in default when no
+ *   model is loaded).
+ * gb_autotune_time(dtype, side, uplo, trans, diag, m, n, alpha, A, lda, B,
+ *   ldb, plans, nplans, reps, ms_out, stream): median of `reps` CUDA-event
+ *   timings of each plan on the caller's buffers (dtype 0 FP64 / 1 FP32);
+ *   B is restored to its input values afterwards.  Synchronous.
+ * gb_autotune(..., best, best_ms, stream): exhaustive search over the
+ *   candidate set (3 repetitions each), the fastest plan and its time.
+ */
+int gb_plan_candidates(int dtype, gb_plan *out, int cap);
+int gb_plan_features(int dtype, int side, int uplo, int trans, int64_t m,
+                     int64_t n, const gb_plan *plan, float *features);
+int gb_plan_set_model(const char *path);
+int gb_plan_choose(int dtype, int side, int uplo, int trans, int64_t m,
+                   int64_t n, gb_plan *plan_out, double *predicted_ms);
+int gb_autotune_time(int dtype, int side, int uplo, int trans, int diag,
+                     int64_t m, int64_t n, double alpha, const void *A,
+                     int64_t lda, void *B, int64_t ldb, const gb_plan *plans,
+                     int nplans, int reps, double *ms_out, void *stream);
+int gb_autotune(int dtype, int side, int uplo, int trans, int diag, int64_t m,
+                int64_t n, double alpha, const void *A, int64_t lda, void *B,
+                int64_t ldb, gb_plan *best, double *best_ms, void *stream);
+
+/*
+ * Cost-model network kernels (FP32, 3 hidden layers of 64, GELU), on device
+ * arrays; `in_dim` = D inputs per sample (1..64), parameters laid out as
+ * W1[64][D], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], w4[64], b4.
+ * gb_mlp_param_count(D): number of parameters (-1 if D < 1).
+ * gb_mlp_forward(params, D, X[n][D], n, Y[n], Z, stream): predictions; when
+ *   Z != NULL also the pre-activations Z[n][3][64] needed by the backward.
+ * gb_mlp_backward(params, D, X, Z, dY[n], n, grads, stream): ADDS the
+ *   gradient of sum_s dY[s] y_s to grads (zero it first).
+ * gb_mlp_loss(Y, T, n, dY, loss, stream): mean squared error; writes
+ *   dY = 2 (Y - T) / n and adds the loss to *loss (device scalar, may be
+ *   NULL).
+ * gb_mlp_adam(params, grads, m, v, np, lr, beta1, beta2, eps, step, stream):
+ *   one Adam step with bias correction (step >= 1).
+ * All asynchronous; negative status = invalid argument.
+ */
+int64_t gb_mlp_param_count(int in_dim);
+int gb_mlp_forward(const float *params, int in_dim, const float *X, int64_t n,
+                   float *Y, float *Z, void *stream);
+int gb_mlp_backward(const float *params, int in_dim, const float *X,
+                    const float *Z, const float *dY, int64_t n, float *grads,
+                    void *stream);
+int gb_mlp_loss(const float *Y, const float *T, int64_t n, float *dY,
+                float *loss, void *stream);
+int gb_mlp_adam(float *params, const float *grads, float *m, float *v,
+                int64_t np, float lr, float beta1, float beta2, float eps,
+                int step, void *stream);
+
+/*
  * gb_plan_counts: host-only description of the launches a plan issues for a
  * triangle of order k (no GPU work).  Writes the number of diagonal-block
  * solves and of GEMM updates, and the sum over GEMMs of M*N*K / ncols (i.e.

@@ -40,6 +40,13 @@ def lib():
         l.oracle_dresidual.restype = ip
         l.oracle_max_threads.argtypes = []
         l.oracle_max_threads.restype = ip
+        pf = ctypes.POINTER(ctypes.c_float)
+        l.oracle_mlp_param_count.argtypes = [ip]
+        l.oracle_mlp_param_count.restype = i64
+        l.oracle_mlp_loss_grad.argtypes = [pf, ip, pf, pf, i64, pd, pd]
+        l.oracle_mlp_loss_grad.restype = dbl
+        l.oracle_adam.argtypes = [pd, pd, pd, pd, i64, dbl, dbl, dbl, dbl, ip]
+        l.oracle_adam.restype = None
         _lib = l
     return _lib
 
@@ -111,3 +118,29 @@ def op_dense(uplo, trans, diag, A, k):
     T = np.where(mask, A, 0.0)
     T[np.diag_indices(k)] = 1.0 if diag == 1 else np.diagonal(A)
     return T.T.copy() if trans == 1 else T
+
+
+# ---- cost-model network (FP64) ---------------------------------------------------
+
+def mlp_param_count(D):
+    return lib().oracle_mlp_param_count(D)
+
+
+def mlp_loss_grad(params, X, T, want_grad=True):
+    """(loss, predictions, gradient) of the 3 x 64 GELU network, FP64."""
+    P = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    n, D = X.shape
+    y = np.zeros(n)
+    g = np.zeros(P.size) if want_grad else None
+    pf = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))  # noqa: E731
+    loss = lib().oracle_mlp_loss_grad(pf(P), D, pf(X), pf(T), n, _ptr(y), _ptr(g) if want_grad else None)
+    return loss, y, g
+
+
+def adam_step(p, g, m, v, lr, b1, b2, eps, step):
+    """One FP64 Adam step, in place on float64 arrays p, m, v."""
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().oracle_adam(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.size, lr, b1, b2, eps, step)

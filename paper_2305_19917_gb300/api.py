@@ -60,6 +60,19 @@ _SIGS = {
     "gb_batched_plan_destroy": ([vp], i32),
     "gb_batched_plan_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
                               ctypes.POINTER(dbl)], i32),
+    "gb_plan_candidates": ([i32, ctypes.POINTER(GbPlan), i32], i32),
+    "gb_plan_features": ([i32, i32, i32, i32, i64, i64, ctypes.POINTER(GbPlan), ctypes.POINTER(flt)], i32),
+    "gb_plan_set_model": ([ctypes.c_char_p], i32),
+    "gb_plan_choose": ([i32, i32, i32, i32, i64, i64, ctypes.POINTER(GbPlan), ctypes.POINTER(dbl)], i32),
+    "gb_autotune_time": ([i32, i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, ctypes.POINTER(GbPlan), i32,
+                          i32, ctypes.POINTER(dbl), vp], i32),
+    "gb_autotune": ([i32, i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, ctypes.POINTER(GbPlan),
+                     ctypes.POINTER(dbl), vp], i32),
+    "gb_mlp_param_count": ([i32], i64),
+    "gb_mlp_forward": ([vp, i32, vp, i64, vp, vp, vp], i32),
+    "gb_mlp_backward": ([vp, i32, vp, vp, vp, i64, vp, vp], i32),
+    "gb_mlp_loss": ([vp, vp, i64, vp, vp, vp], i32),
+    "gb_mlp_adam": ([vp, vp, vp, vp, i64, flt, flt, flt, flt, i32, vp], i32),
     "gb_mixed_history": ([ctypes.POINTER(dbl), ctypes.POINTER(i32), i32], i32),
     "gb_bf16_gemm_update": ([i64, i64, i64, vp, i64, vp, i64, vp, i64, flt, vp], i32),
     "gb_device_status": ([i32], i32),
@@ -210,6 +223,70 @@ class BatchedPlan:
             self.close()
         except Exception:
             pass
+
+
+def gb_plan_candidates(dtype=0):
+    arr = (GbPlan * 64)()
+    n = lib().gb_plan_candidates(dtype, arr, 64)
+    return [dict(driver=arr[i].driver, nb=arr[i].nb, depth=arr[i].depth) for i in range(n)]
+
+
+N_FEATURES = 17
+
+
+def gb_plan_features(dtype, side, uplo, trans, m, n, plan):
+    f = (flt * N_FEATURES)()
+    lib().gb_plan_features(dtype, side, uplo, trans, m, n, _plan_ptr(plan), f)
+    return list(f)
+
+
+def gb_plan_set_model(path):
+    return lib().gb_plan_set_model(None if path is None else str(path).encode())
+
+
+def gb_plan_choose(dtype, side, uplo, trans, m, n):
+    p, ms = GbPlan(), dbl()
+    st = lib().gb_plan_choose(dtype, side, uplo, trans, m, n, ctypes.byref(p), ctypes.byref(ms))
+    return st, dict(driver=p.driver, nb=p.nb, depth=p.depth), ms.value
+
+
+def gb_autotune_time(dtype, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, plans, reps=2, stream=0):
+    arr = (GbPlan * len(plans))(*[GbPlan(p["driver"], p["nb"], p["depth"], 0) for p in plans])
+    out = (dbl * len(plans))()
+    st = lib().gb_autotune_time(dtype, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, arr, len(plans),
+                                reps, out, stream or None)
+    if st != 0:
+        raise GbError("gb_autotune_time", st)
+    return list(out)
+
+
+def gb_autotune(dtype, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream=0):
+    p, ms = GbPlan(), dbl()
+    st = lib().gb_autotune(dtype, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, ctypes.byref(p),
+                           ctypes.byref(ms), stream or None)
+    if st != 0:
+        raise GbError("gb_autotune", st)
+    return dict(driver=p.driver, nb=p.nb, depth=p.depth), ms.value
+
+
+def gb_mlp_param_count(in_dim):
+    return lib().gb_mlp_param_count(in_dim)
+
+
+def gb_mlp_forward(params, in_dim, X, n, Y, Z=0, stream=0):
+    return lib().gb_mlp_forward(params, in_dim, X, n, Y, Z or None, stream or None)
+
+
+def gb_mlp_backward(params, in_dim, X, Z, dY, n, grads, stream=0):
+    return lib().gb_mlp_backward(params, in_dim, X, Z, dY, n, grads, stream or None)
+
+
+def gb_mlp_loss(Y, T, n, dY, loss=0, stream=0):
+    return lib().gb_mlp_loss(Y, T, n, dY, loss or None, stream or None)
+
+
+def gb_mlp_adam(params, grads, m, v, np_, lr, beta1, beta2, eps, step, stream=0):
+    return lib().gb_mlp_adam(params, grads, m, v, np_, lr, beta1, beta2, eps, step, stream or None)
 
 
 def gb_mixed_history(cap=64):

@@ -24,5 +24,7 @@ inline bool plan_valid(const gb_plan &p)
 // Planner: the loaded cost model's argmin if one is loaded, else the
 // built-in default (defined in plan.cu).
 gb_plan choose_plan(int dtype, int side, int uplo, int trans, int64_t m, int64_t n);
+int plan_candidates(int dtype, gb_plan *out, int cap);
+void plan_features(int dtype, int side, int uplo, int trans, int64_t m, int64_t n, const gb_plan &p, float *f);
 
 }  // namespace gb
