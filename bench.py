@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--path", default="mixed", choices=["mixed", "fp64", "batched"])
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="batched path precision")
+    p.add_argument("--prec", default="bf16", choices=["bf16", "fp8"], help="mixed path low precision")
     p.add_argument("--count", type=int, default=4096, help="batched path: number of problems")
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -232,7 +233,8 @@ def run_ours(args):
     api.lib()
     m, n = args.m, args.n
     side, uplo, trans, diag, alpha = 0, 0, 0, 0, 1.5
-    tol, max_iter = 1e-11, 30
+    tol, max_iter = 1e-11, 60
+    prec = api.PREC_FP8 if args.prec == "fp8" else api.PREC_BF16
 
     # Host inputs (seeded), device copies.
     A_h, B_h = inputs.make_problem(side, uplo, trans, diag, m, n, seed=0)
@@ -247,7 +249,7 @@ def run_ours(args):
         B.copy_(B0)
 
     def solve_mixed():
-        st, it, est = api.trsm_mixed(side, uplo, trans, diag, alpha, A, B, tol=tol, max_iter=max_iter,
+        st, it, est = api.trsm_mixed(side, uplo, trans, diag, alpha, A, B, tol=tol, prec=prec, max_iter=max_iter,
                                      stream=stream)
         return st, it, est, api.gb_mixed_history()
 
@@ -314,7 +316,8 @@ def run_ours(args):
         A_e.copy_(A_pin, non_blocking=True)
         B.copy_(B_pin, non_blocking=True)
         if mixed:
-            api.trsm_mixed(side, uplo, trans, diag, alpha, A_e, B, tol=tol, max_iter=max_iter, stream=stream)
+            api.trsm_mixed(side, uplo, trans, diag, alpha, A_e, B, tol=tol, prec=prec, max_iter=max_iter,
+                           stream=stream)
         else:
             api.trsm(side, uplo, trans, diag, alpha, A_e, B, stream=stream)
         X_pin.copy_(B, non_blocking=True)
@@ -365,7 +368,7 @@ def run_ours(args):
 
     if rank == 0:
         if mixed:
-            wl = (f"mixed BF16 + refinement TRSM Left/Lower/N/NonUnit m=n={m} to FP64-level error "
+            wl = (f"mixed {args.prec.upper()} + refinement TRSM Left/Lower/N/NonUnit m=n={m} to FP64-level error "
                   f"(tol {tol:g} on ||D||/||X||; forward error vs FP64 oracle <= 1e-10), alpha=1.5, "
                   f"diag U[1,2), offdiag U(-1,1)/m, B~N(0,1), seed 0")
         else:
@@ -374,7 +377,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16+f64" if mixed else "f64", "data": "synthetic",
+                "dtype": (args.prec + "+f64") if mixed else "f64", "data": "synthetic",
                 "config": {"workload": wl, "global_batch": world,
                            "l2": "inputs larger than L2 (4 GiB); B re-copied before each step"},
                 "roofline": roofline, "cpu_baseline": cpu,

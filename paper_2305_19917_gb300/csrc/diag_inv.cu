@@ -10,6 +10,7 @@
 // Storage ("band"): block b occupies band[(b*128 + c)*128 + i] = L_b(i, c),
 // i.e. each block column-major with leading dimension 128.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include "common.cuh"
 
 namespace gb {
@@ -59,9 +60,13 @@ __global__ void __launch_bounds__(NBI) invert_blocks_kernel(const float *__restr
 // plus the BF16 copy.  256 threads, each an 8 x 4 register tile: rows
 // ty*4 .. +3 and 64 + ty*4 .. +3, columns tx*4 .. +3.
 constexpr int AC = 64;  // columns per CTA
+// FP8 = true: instead of the BF16 copy, an FP8 (E4M3) copy Y8 with one
+// power-of-two scale for the CTA's 128 x 64 block (written to *s8 + blockIdx.x).
+template <bool FP8>
 __global__ void __launch_bounds__(256)
 apply_inverse_kernel(const float *__restrict__ Linv, float *__restrict__ Y, int64_t ldy,
-                     __nv_bfloat16 *__restrict__ Ybf, int nr, int64_t ncols)
+                     __nv_bfloat16 *__restrict__ Ybf, int nr, int64_t ncols, uint8_t *__restrict__ Y8,
+                     float *__restrict__ s8)
 {
     extern __shared__ __align__(16) float sm[];
     float *Ls = sm;                 // Ls[k*NBI + i] = Linv(i, k)   (column k contiguous)
@@ -107,12 +112,30 @@ apply_inverse_kernel(const float *__restrict__ Linv, float *__restrict__ Y, int6
         for (int c = 0; c < 4; c++) Ys[i * LDY + cc + c] = acc[r][c];
     }
     __syncthreads();
+    float scale_inv = 1.f;
+    if (FP8) {
+        // block maximum -> power-of-two scale s with amax / s <= 448
+        __shared__ float red[8];
+        float mx = 0.f;
+        for (int idx = tid; idx < NBI * AC; idx += 256) mx = fmaxf(mx, fabsf(Ys[(idx % NBI) * LDY + idx / NBI]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0) red[tid >> 5] = mx;
+        __syncthreads();
+        mx = 0.f;
+        for (int w = 0; w < 8; w++) mx = fmaxf(mx, red[w]);
+        const float sc = mx > 0.f ? exp2f(ceilf(log2f(mx / 448.f))) : 1.f;
+        scale_inv = 1.f / sc;
+        if (tid == 0) s8[blockIdx.x] = sc;
+    }
     for (int idx = tid; idx < NBI * AC; idx += 256) {
         const int i = idx % NBI, c = idx / NBI;
         if (i < nr && c0 + c < ncols) {
             const float v = Ys[i * LDY + c];
             Y[i + (c0 + c) * ldy] = v;
-            Ybf[i + (c0 + c) * ldy] = __float2bfloat16_rn(v);
+            if (FP8)
+                Y8[i + (c0 + c) * ldy] = __nv_cvt_float_to_fp8(v * scale_inv, __NV_SATFINITE, __NV_E4M3);
+            else
+                Ybf[i + (c0 + c) * ldy] = __float2bfloat16_rn(v);
         }
     }
 }
@@ -128,7 +151,9 @@ int diag_inv_prepare()
     if (!done) {
         GB_CUDA(cudaFuncSetAttribute(invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)INV_SMEM));
-        GB_CUDA(cudaFuncSetAttribute(apply_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GB_CUDA(cudaFuncSetAttribute(apply_inverse_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)APPLY_SMEM));
+        GB_CUDA(cudaFuncSetAttribute(apply_inverse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)APPLY_SMEM));
         done = true;
     }
@@ -154,7 +179,23 @@ int launch_apply_inverse(const float *Linv_b, float *Yb, int64_t ldy, __nv_bfloa
     GB_TRY(diag_inv_prepare());
     const int64_t grid = (ncols + AC - 1) / AC;
     LaunchScope ls(KK_DIAG, s, double(nr) * nr * ncols, 4.0 * (double(nr) * nr + 2.0 * nr * ncols) + 2.0 * nr * ncols);
-    apply_inverse_kernel<<<(unsigned)grid, 256, APPLY_SMEM, s>>>(Linv_b, Yb, ldy, Ybf_b, nr, ncols);
+    apply_inverse_kernel<false><<<(unsigned)grid, 256, APPLY_SMEM, s>>>(Linv_b, Yb, ldy, Ybf_b, nr, ncols,
+                                                                         nullptr, nullptr);
+    return check(cudaGetLastError());
+}
+
+// As above, emitting the FP8 copy Y8_b (same layout) and the block scales
+// s8_b[j] of the 128 x 64 blocks j = 0, 1, ... of this row block.
+int launch_apply_inverse_fp8(const float *Linv_b, float *Yb, int64_t ldy, uint8_t *Y8_b, float *s8_b, int nr,
+                             int64_t ncols, cudaStream_t s)
+{
+    if (nr <= 0 || ncols <= 0) return 0;
+    if (nr > NBI) return GB_STATUS_CUDA_ERROR;
+    GB_TRY(diag_inv_prepare());
+    const int64_t grid = (ncols + AC - 1) / AC;
+    LaunchScope ls(KK_DIAG, s, double(nr) * nr * ncols, 4.0 * (double(nr) * nr + 2.0 * nr * ncols) + 1.0 * nr * ncols);
+    apply_inverse_kernel<true><<<(unsigned)grid, 256, APPLY_SMEM, s>>>(Linv_b, Yb, ldy, nullptr, nr, ncols, Y8_b,
+                                                                        s8_b);
     return check(cudaGetLastError());
 }
 

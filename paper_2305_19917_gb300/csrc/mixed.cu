@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include "common.cuh"
 #include "driver.cuh"
 #include "mixed.cuh"
@@ -36,6 +37,12 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
                        const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
                        cudaStream_t s, int *status);
 int tc_gemm_prepare();
+int tc_gemm_fp8_prepare();
+int launch_tc_gemm_fp8(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
+                       float *C, int64_t ldc, float alpha, const float *sA, int64_t ldsa, const float *sB,
+                       int64_t ldsb, cudaStream_t s, int *status);
+int launch_apply_inverse_fp8(const float *Linv_b, float *Yb, int64_t ldy, uint8_t *Y8_b, float *s8_b, int nr,
+                             int64_t ncols, cudaStream_t s);
 int diag_inv_prepare();
 int launch_invert_blocks(const float *band, float *inv, int64_t nblocks, cudaStream_t s);
 int launch_apply_inverse(const float *Linv_b, float *Yb, int64_t ldy, __nv_bfloat16 *Ybf_b, int nr, int64_t ncols,
@@ -98,9 +105,13 @@ __device__ __forceinline__ int bexp(double a)
 // strictly lower part only, so that small off-diagonal entries keep all their
 // digits when the diagonal is much larger (the diagonal is applied exactly in
 // FP64 by the residual kernel).  Integer arithmetic on the exponent fields.
-__global__ void __launch_bounds__(256) rowexp_kernel(View v, int64_t kp, int *e_row)
+// With bmax != nullptr also the maxima |a| of the strictly-lower 128 x 128
+// blocks (as FP32 bit patterns, which order like the values), for the FP8
+// block scales.
+__global__ void __launch_bounds__(256) rowexp_kernel(View v, int64_t kp, int *e_row, unsigned *bmax)
 {
     __shared__ double t[64][65];
+    __shared__ float red[8];
     const int64_t i0 = int64_t(blockIdx.y) * 64, c0 = int64_t(blockIdx.x) * 64;
     if (c0 > i0 + 63) return;
     load_tile(v, i0, c0, t);
@@ -111,6 +122,27 @@ __global__ void __launch_bounds__(256) rowexp_kernel(View v, int64_t kp, int *e_
         for (int c = 0; c < 64; c++)
             if (c0 + c != i0 + tid) mx = max(mx, bexp(t[tid][c]));
         if (mx > 0) atomicMax(&e_row[i0 + tid], mx - 1023 + 2);
+    }
+    if (bmax && (c0 >> 7) < (i0 >> 7)) {
+        float m = 0.f;
+        for (int idx = tid; idx < 64 * 64; idx += 256) m = fmaxf(m, fabsf(float(t[idx >> 6][idx & 63])));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((tid & 31) == 0) red[tid >> 5] = m;
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < 8; w++) m = fmaxf(m, red[w]);
+            atomicMax(&bmax[(i0 >> 7) * (kp >> 7) + (c0 >> 7)], __float_as_uint(m));
+        }
+    }
+}
+
+// Power-of-two FP8 block scales s = 2^ceil(log2(amax / 448)) (1 for zero
+// blocks), so that every scaled entry fits E4M3's largest finite value.
+__global__ void block_scales_kernel(const unsigned *bmax, float *bscale, int64_t nb)
+{
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nb; i += int64_t(gridDim.x) * blockDim.x) {
+        const float m = __uint_as_float(bmax[i]);
+        bscale[i] = m > 0.f ? exp2f(ceilf(log2f(m / 448.f))) : 1.f;
     }
 }
 
@@ -164,7 +196,7 @@ __device__ __forceinline__ long long fixed42(double a, int e)
 // lower part, the FP64 diagonal and the FP32 band of diagonal 64-blocks.
 __global__ void __launch_bounds__(256)
 prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bfloat16 *As, float *band,
-             double *dg)
+             double *dg, uint8_t *A8, const float *bscale)
 {
     __shared__ double t[64][65];
     const int64_t i0 = int64_t(blockIdx.y) * 64, c0 = int64_t(blockIdx.x) * 64;
@@ -179,6 +211,9 @@ prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bflo
         double a = t[li][lc];
         size_t off = size_t(i) * size_t(kp) + size_t(c);
         Abf[off] = d2bf16(a);
+        if (A8 && (c >> 7) < (i >> 7))
+            A8[off] = __nv_cvt_float_to_fp8(float(a) / bscale[(i >> 7) * (kp >> 7) + (c >> 7)], __NV_SATFINITE,
+                                            __NV_E4M3);
         // balanced base-64 digits of N = round(a 2^(42-e)): N = sum_p q_p 64^(7-p),
         // q_p in [-32, 32]; least significant first
         long long N = (c == i) ? 0 : fixed42(a, e_row[i]);
@@ -351,6 +386,11 @@ struct LowExec {
     int64_t kp, np;
     cudaStream_t s;
     int *status_word;   // device word for wait timeouts (nullptr = library's own)
+    bool fp8 = false;   // FP8 E4M3 updates with block scales instead of BF16
+    const uint8_t *A8 = nullptr;
+    const float *sA = nullptr;   // (kp/128)^2 block scales of A8
+    uint8_t *Y8 = nullptr;
+    float *sY = nullptr;         // (kp/128) x (np/64) block scales of Y8
     int status = 0;
     bool ok() const { return status == 0; }
     void ts(int64_t b0, int64_t nr, float a)
@@ -361,13 +401,22 @@ struct LowExec {
             return;
         }
         // TS task: X_b = L_b^-1 Y_b with the precomputed inverse of the block
-        status = launch_apply_inverse(binv + b0 * kBand, Y + b0, kp, Ybf + b0, (int)nr, np, s);
+        if (fp8)
+            status = launch_apply_inverse_fp8(binv + b0 * kBand, Y + b0, kp, Y8 + b0, sY + (b0 / 128) * (np / 64),
+                                              (int)nr, np, s);
+        else
+            status = launch_apply_inverse(binv + b0 * kBand, Y + b0, kp, Ybf + b0, (int)nr, np, s);
     }
     void gemm(int64_t ci0, int64_t M, int64_t ak0, int64_t K, float a)
     {
         if (status) return;
-        status = launch_tc_gemm_bf16(M, np, K, Abf + ci0 * kp + ak0, kp, Ybf + ak0, kp, Y + ci0, kp, a, s,
-                                     status_word);
+        if (fp8)
+            status = launch_tc_gemm_fp8(M, np, K, A8 + ci0 * kp + ak0, kp, Y8 + ak0, kp, Y + ci0, kp, a,
+                                        sA + (ci0 / 128) * (kp / 128) + ak0 / 128, kp / 128,
+                                        sY + (ak0 / 128) * (np / 64), np / 64, s, status_word);
+        else
+            status = launch_tc_gemm_bf16(M, np, K, Abf + ci0 * kp + ak0, kp, Ybf + ak0, kp, Y + ci0, kp, a, s,
+                                         status_word);
     }
 };
 
@@ -412,6 +461,7 @@ struct LowGraph {
     cudaGraphExec_t exec = nullptr;
     const void *ws = nullptr;
     int64_t kp = 0, np = 0;
+    bool fp8 = false;
     uint64_t nkernels = 0;
 };
 
@@ -423,7 +473,7 @@ int low_graph(LowExec &le, const void *ws, LowGraph **out)
     GB_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return GB_STATUS_CUDA_ERROR;
     LowGraph &g = cache[dev];
-    if (g.exec && g.ws == ws && g.kp == le.kp && g.np == le.np) {
+    if (g.exec && g.ws == ws && g.kp == le.kp && g.np == le.np && g.fp8 == le.fp8) {
         *out = &g;
         return 0;
     }
@@ -434,6 +484,7 @@ int low_graph(LowExec &le, const void *ws, LowGraph **out)
     if (!cap_stream[dev]) GB_CUDA(cudaStreamCreateWithFlags(&cap_stream[dev], cudaStreamNonBlocking));
     // everything that allocates or sets attributes happens before capture
     GB_TRY(tc_gemm_prepare());
+    GB_TRY(tc_gemm_fp8_prepare());
     GB_TRY(diag_inv_prepare());
     cudaStream_t user = le.s;
     le.s = cap_stream[dev];
@@ -455,6 +506,7 @@ int low_graph(LowExec &le, const void *ws, LowGraph **out)
     g.ws = ws;
     g.kp = le.kp;
     g.np = le.np;
+    g.fp8 = le.fp8;
     g.nkernels = capture_count() - before;
     *out = &g;
     return 0;
@@ -468,7 +520,7 @@ static thread_local double tl_rho[64];
 static thread_local int tl_levels[64];
 static thread_local int tl_nhist = 0;
 
-MixedLayout mixed_layout(int side, int64_t m, int64_t n)
+MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec)
 {
     MixedLayout L;
     const int64_t k = side == GB_LEFT ? m : n;
@@ -496,20 +548,36 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n)
     L.o_norm = take(64);
     L.o_dg = take(size_t(L.kp) * 8);
     L.o_xm = take(size_t(L.np) * 4);
+    if (prec == GB_PREC_FP8) {
+        const size_t nbk = size_t(L.kp / 128);
+        L.o_a8 = take(kk);
+        L.o_bmax = take(nbk * nbk * 4);
+        L.o_bscale = take(nbk * nbk * 4);
+        L.o_y8 = take(kn);
+        L.o_sy = take(nbk * size_t(L.np / 64) * 4);
+    } else {
+        L.o_a8 = L.o_bmax = L.o_bscale = L.o_y8 = L.o_sy = 0;
+    }
     L.total = off;
     return L;
 }
 
 int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
-               int64_t lda, double *B, int64_t ldb, double tol, int max_iter, int *iters_out, double *est_err_out,
-               cudaStream_t s, char *ws, int *status_word, bool use_graph)
+               int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
+               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph)
 {
     const int64_t k = side == GB_LEFT ? m : n;
     const int64_t ncols = side == GB_LEFT ? n : m;
     const bool mt = side == GB_LEFT ? (trans == GB_TRANS) : (trans == GB_NOTRANS);
     const bool forward = (uplo == GB_LOWER) != mt;
-    const MixedLayout L = mixed_layout(side, m, n);
+    const MixedLayout L = mixed_layout(side, m, n, prec);
     const int64_t kp = L.kp, np = L.np;
+    const bool fp8 = prec == GB_PREC_FP8;
+    uint8_t *A8 = fp8 ? reinterpret_cast<uint8_t *>(ws + L.o_a8) : nullptr;
+    unsigned *bmax = fp8 ? reinterpret_cast<unsigned *>(ws + L.o_bmax) : nullptr;
+    float *bscale = fp8 ? reinterpret_cast<float *>(ws + L.o_bscale) : nullptr;
+    uint8_t *Y8 = fp8 ? reinterpret_cast<uint8_t *>(ws + L.o_y8) : nullptr;
+    float *sY = fp8 ? reinterpret_cast<float *>(ws + L.o_sy) : nullptr;
     const size_t kn = size_t(kp) * size_t(np);
 
     View v{A, lda, mt, !forward, diag == GB_UNIT, k};
@@ -542,12 +610,18 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
         dim3 tgrid((unsigned)(kp / 64), (unsigned)(kp / 64));
         {
             LaunchScope ls(KK_CONVERT, s, 0, 8.0 * double(k) * double(k) / 2);
-            rowexp_kernel<<<tgrid, 256, 0, s>>>(v, kp, e_row);
+            if (fp8 && (st = check(cudaMemsetAsync(bmax, 0, size_t(kp / 128) * (kp / 128) * 4, s)))) break;
+            rowexp_kernel<<<tgrid, 256, 0, s>>>(v, kp, e_row, bmax);
             if ((st = check(cudaGetLastError()))) break;
         }
         {
             LaunchScope ls(KK_CONVERT, s, 0, (8.0 + 2.0 * (1 + kSlices)) * double(kp) * double(kp) / 2);
-            prepA_kernel<<<tgrid, 256, 0, s>>>(v, kp, e_row, Abf, As, band, dg);
+            if (fp8) {
+                const int64_t nbb = (kp / 128) * (kp / 128);
+                block_scales_kernel<<<(unsigned)((nbb + 255) / 256), 256, 0, s>>>(bmax, bscale, nbb);
+                if ((st = check(cudaGetLastError()))) break;
+            }
+            prepA_kernel<<<tgrid, 256, 0, s>>>(v, kp, e_row, Abf, As, band, dg, A8, bscale);
             if ((st = check(cudaGetLastError()))) break;
         }
         {
@@ -558,6 +632,11 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
         }
         if ((st = launch_invert_blocks(band, binv, kp / kBand, s))) break;
         LowExec le{Y, Ybf, Abf, binv, kp, np, s, status_word};
+        le.fp8 = fp8;
+        le.A8 = A8;
+        le.sA = bscale;
+        le.Y8 = Y8;
+        le.sY = sY;
         LowGraph *lg = nullptr;
         if (use_graph && (st = low_graph(le, ws, &lg))) break;
         const int64_t nel = int64_t(kn);
@@ -631,14 +710,13 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
                      int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
                      double *est_err_out, cudaStream_t s)
 {
-    (void)prec;
-    const MixedLayout L = mixed_layout(side, m, n);
+    const MixedLayout L = mixed_layout(side, m, n, prec);
     cudaMemPool_t pool = library_pool();
     if (!pool) return GB_STATUS_CUDA_ERROR;
     char *ws = nullptr;
     GB_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&ws), L.total, pool, s));
-    const int st = mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, max_iter, iters_out,
-                              est_err_out, s, ws, nullptr, true);
+    const int st = mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
+                              iters_out, est_err_out, s, ws, nullptr, true);
     cudaFreeAsync(ws, s);
     return st;
 }
@@ -672,7 +750,7 @@ int mixed_validate(int side, int uplo, int trans, int diag, int64_t m, int64_t n
     if (B == nullptr && !empty) return -10;
     if (ldb < (m > 1 ? m : 1)) return -11;
     if (!(tol >= 0.0)) return -12;
-    if (prec != GB_PREC_BF16) return -13;
+    if (prec != GB_PREC_BF16 && prec != GB_PREC_FP8) return -13;
     if (max_iter < 1 || max_iter > 1000) return -14;
     return 0;
 }

@@ -12,9 +12,10 @@ namespace gb {
 struct MixedLayout {
     int64_t kp, np;
     size_t o_abf, o_as, o_band, o_binv, o_r, o_x, o_y, o_ybf, o_zs, o_e, o_f, o_norm, o_dg, o_xm;
+    size_t o_a8, o_bmax, o_bscale, o_y8, o_sy;  // FP8 variant only (0 otherwise)
     size_t total;
 };
-MixedLayout mixed_layout(int side, int64_t m, int64_t n);
+MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec);
 
 // The refinement solve on a caller-provided work space `ws` (layout above,
 // 256-byte aligned), with `status_word` as the device word for wait
@@ -22,8 +23,8 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n);
 // replayed from a cached CUDA graph (use_graph) or launched directly.
 // Arguments are assumed valid; alpha != 0; m, n > 0.  Synchronous.
 int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
-               int64_t lda, double *B, int64_t ldb, double tol, int max_iter, int *iters_out, double *est_err_out,
-               cudaStream_t s, char *ws, int *status_word, bool use_graph);
+               int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
+               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph);
 
 // Argument checks of gb_dtrsm_mixed (0 or -i).
 int mixed_validate(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,

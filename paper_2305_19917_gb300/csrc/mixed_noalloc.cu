@@ -78,13 +78,13 @@ extern "C" int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag, i
         if (st) return st;
         return gb::check(cudaStreamSynchronize(s));
     }
-    const gb::MixedLayout L = gb::mixed_layout(side, m, n);
+    const gb::MixedLayout L = gb::mixed_layout(side, m, n, prec);
     if (L.total + gb::kStatusBytes > gb::kNoAllocBytes) return GB_STATUS_SCRATCH_TOO_SMALL;
     char *base = nullptr;
     GB_TRY(gb::scratch_address(&base));
     int *status_word = reinterpret_cast<int *>(base);
     GB_CUDA(cudaMemsetAsync(status_word, 0, sizeof(int), s));
-    int st = gb::mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, max_iter, iters_out,
+    int st = gb::mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, iters_out,
                             est_err_out, s, base + gb::kStatusBytes, status_word, false);
     if (st == 0 || st == GB_STATUS_NOT_CONVERGED) {
         int h = 0;

@@ -86,3 +86,20 @@ def test_mixed_config_scale_sampled(m, n):
     X = Bd[:, cols].cpu().numpy()
     Xo = oracle.dtrsm(0, 0, 0, 0, 1.5, A, B[:, cols])
     assert fwd_err(X, Xo) <= 1e-10
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", [(0, 0, 0, 0), (1, 1, 1, 0), (0, 1, 0, 1), (1, 0, 1, 1)])
+def test_mixed_fp8_block_scaled_updates(side, uplo, trans, diag):
+    """FP8 E4M3 GEMM updates with per-block power-of-two scales: the
+    refinement still reaches the FP64-level tolerance (more steps than BF16)."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    m, n = 600, 300
+    A, B = inputs.make_problem(side, uplo, trans, diag, m, n, seed=21)
+    Xo = oracle.dtrsm(side, uplo, trans, diag, 1.5, A, B)
+    Ad = api.to_device_colmajor(A, torch.float64)
+    Bd = api.to_device_colmajor(B, torch.float64)
+    st, it, est = api.trsm_mixed(side, uplo, trans, diag, 1.5, Ad, Bd, tol=1e-11, prec=api.PREC_FP8, max_iter=60)
+    torch.cuda.synchronize()
+    assert st == 0 and it <= 40, (st, it, est, api.gb_mixed_history())
+    assert fwd_err(Bd.cpu().numpy(), Xo) <= 1e-10
