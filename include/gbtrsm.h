@@ -168,8 +168,9 @@ int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag,
 /*
  * gb_mixed_history: refinement history of the last gb_dtrsm_mixed call made
  * by this host thread.  Writes up to `cap` entries: rho[t] = ||D||_F/||X||_F
- * of correction t+1 and levels[t] = the number of 6-bit digit levels the
- * residual preceding that correction used (either pointer may be NULL).
+ * of correction t+1 and levels[t] = 10 P + P2 for the residual preceding
+ * that correction (it formed A digit slices 1..P with the first correction
+ * digit and 1..P2 also with the second; either pointer may be NULL).
  * Returns the number of corrections recorded.  Host only.
  */
 int gb_mixed_history(double *rho, int *levels, int cap);

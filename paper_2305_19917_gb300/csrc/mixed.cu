@@ -9,7 +9,7 @@
 //   until ||D||_F <= tol ||X||_F.
 //
 // The residual is carried incrementally: after X += D~ (D~ = D rounded to
-// the two 6-bit digits per column that the residual kernel consumes),
+// the two 8-bit digits per column that the residual kernel consumes),
 // R -= Mv D~, so R stays the residual of the X actually held.  Mv is cut
 // without its diagonal into seven 6-bit digit slices with a power-of-two
 // scale per row (42 bits of the largest off-diagonal entry); the diagonal
@@ -34,8 +34,8 @@ namespace gb {
 int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
                         int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s, int *status);
 int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
-                       const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
-                       cudaStream_t s, int *status);
+                       const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int P,
+                       int P2, cudaStream_t s, int *status);
 int tc_gemm_prepare();
 int tc_gemm_fp8_prepare();
 int launch_tc_gemm_fp8(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
@@ -283,9 +283,10 @@ writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t
 }
 
 // Per column j: f_j = E + 2 with 2^E <= max_k |Y(k,j)| < 2^(E+1); the
-// 12-bit value N = round(Y 2^(12-f_j)) (|N| <= 2^11, FP32 arithmetic, exact
-// scaling) split into balanced base-64 digits z_1, z_2 (N = 64 z_1 + z_2);
-// X += D~ with D~ = N 2^(f_j-12) (exact in FP32, added in FP64).
+// 16-bit value N = round(Y 2^(16-f_j)) (|N| <= 2^15, FP32 arithmetic, exact
+// scaling) split into balanced base-256 digits z_1, z_2 (N = 256 z_1 + z_2,
+// |z_q| <= 128, exact in BF16); X += D~ with D~ = N 2^(f_j-16) (exact in
+// FP32, added in FP64).
 // Accumulates sum D~^2 into norms[0] (FP32 partial sums), and, on the first
 // call, sum X^2 into norms[1] and the column maxima of |X| into xmax; the
 // largest column ratio max|D~| / max|X| goes to norms[2] (as bits).
@@ -307,15 +308,15 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
     const int be = int((__float_as_uint(mx) >> 23) & 0xFF);
     const int f = (be > 0) ? be - 127 + 2 : 0;
     if (threadIdx.x == 0) f_col[j] = f;
-    const float up = ldexpf(1.0f, 12 - f), down = ldexpf(1.0f, f - 12);
+    const float up = ldexpf(1.0f, 16 - f), down = ldexpf(1.0f, f - 16);
     __nv_bfloat16 *z1 = Zs + j * kp;
     __nv_bfloat16 *z2 = Zs + np * kp + j * kp;
     double *x = X + j * kp;
     float sd = 0.f, sx = 0.f;
     for (int64_t i = threadIdx.x; i < kp; i += 256) {
         const int N = (be > 0) ? __float2int_rn(y[i] * up) : 0;
-        const int q2 = ((N + 32) & 63) - 32;
-        const int q1 = (N - q2) >> 6;
+        const int q2 = ((N + 128) & 255) - 128;
+        const int q1 = (N - q2) >> 8;
         z1[i] = __int2bfloat16_rn(q1);
         z2[i] = __int2bfloat16_rn(q2);
         const float d = float(N) * down;  // exact
@@ -427,28 +428,37 @@ int low_solve(LowExec &e, int64_t kp)
     return e.status;
 }
 
-// Number of 6-bit digit levels the residual must keep for a correction Z
-// whose size relative to X is rho: level L terms (weight 2^(-6L)) sit
-// 2^(-6(L-2)) below the leading one, so dropping the levels above L costs
-// about rho 2^(-6(L-1)) |Mv||X|; that must stay below 2^-target |Mv||X| with
+// Which digit pairs the residual must form for a correction Z whose size
+// relative to X is rho.  Pair (p, q) has weight 2^-(6p + 8q), i.e. it sits
+// 2^-(6p + 8q - 14) below the leading pair (1, 1), and the leading pair is
+// about rho |Mv||X|; every pair above 2^-target |Mv||X| is formed, with
 // target = log2(1/tol) + 2 (a factor 4 under the requested tolerance).
-int levels_for(double rho, double tol)
+// Returns P (slices paired with z_1) and P2 (slices also paired with z_2).
+void pairs_for(double rho, double tol, int *P, int *P2)
 {
-    if (!(rho > 0)) return 2;
     const double target = -std::log2(tol > 0 ? tol : 1e-16) + 2.0;
-    const double b = -std::log2(rho);
-    int L = int(std::ceil((target - b) / 6.0)) + 1;
-    if (L > 8) L = 8;
-    if (L < 2) L = 2;
-    return L;
+    const double b = rho > 0 ? -std::log2(rho) : 1e9;
+    const double budget = target - b + 14.0;
+    int p1 = int(std::floor((budget - 8.0) / 6.0));
+    int p2 = int(std::floor((budget - 16.0) / 6.0));
+    if (p1 > 7) p1 = 7;
+    if (p1 < 1) p1 = 1;
+    if (p2 > p1) p2 = p1;
+    if (p2 < 0) p2 = 0;
+    *P = p1;
+    *P2 = p2;
 }
 
+// One launch per K range of at most 16384 (the int64 sums stay below 2^63);
+// inside, chunks of 4096 keep every tensor-core sum exact (|a| <= 32,
+// |z| <= 128: 4096 * 32 * 128 = 2^24).
 int residual_update(double *R, const __nv_bfloat16 *As, const __nv_bfloat16 *Zs, const int *e_row, const int *f_col,
-                    const double *dg, float *Y, int64_t kp, int64_t np, int Lmax, cudaStream_t s, int *status_word)
+                    const double *dg, float *Y, int64_t kp, int64_t np, int P, int P2, cudaStream_t s,
+                    int *status_word)
 {
     for (int64_t lo = 0; lo < kp; lo += 16384) {
         int64_t hi = lo + 16384 < kp ? lo + 16384 : kp;
-        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, dg, Y, kp, np, lo, hi, Lmax, s, status_word));
+        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, dg, Y, kp, np, lo, hi, P, P2, s, status_word));
     }
     return 0;
 }
@@ -640,7 +650,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
         LowGraph *lg = nullptr;
         if (use_graph && (st = low_graph(le, ws, &lg))) break;
         const int64_t nel = int64_t(kn);
-        int Lmax = 8;
+        int Lmax = 76;
         double nx = 0, prev_rho = 0;
         for (int t = 0;; t++) {
             // Y = float(R) was written by prepB (t = 0) or by the residual kernel
@@ -684,8 +694,10 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
                 if (t >= max_iter) break;
                 prev_rho = rho;
             }
-            Lmax = levels_for(t == 0 ? 1.0 : h_norm[2], tol);
-            if ((st = residual_update(R, As, Zs, e_row, f_col, dg, Y, kp, np, Lmax, s, status_word))) break;
+            int P = 7, P2 = 6;
+            pairs_for(t == 0 ? 1.0 : h_norm[2], tol, &P, &P2);
+            Lmax = P * 10 + P2;  // recorded in the history as 10*P + P2
+            if ((st = residual_update(R, As, Zs, e_row, f_col, dg, Y, kp, np, P, P2, s, status_word))) break;
         }
         if (st) break;
         {

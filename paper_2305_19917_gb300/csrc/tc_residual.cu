@@ -3,24 +3,26 @@
 //     R(i,j) -= sum_k Mv(i,k) Z(k,j)         for the lower-triangular Mv
 //
 // where both factors are given as fixed-point digit slices (BF16 holding
-// small integers, |digit| <= 32), the strictly lower part of Mv as
-//     Mv(i,k) = 2^e_i * sum_{p=1..7} a_p(i,k) 2^(-6p)      (per-row scale)
+// small integers), the strictly lower part of Mv as
+//     Mv(i,k) = 2^e_i * sum_{p=1..7} a_p(i,k) 2^(-6p),   |a_p| <= 32
 // (the diagonal Mv(i,i) is applied separately, in FP64), and
-//     Z(k,j)  = 2^f_j * sum_{q=1..2} z_q(k,j) 2^(-6q)      (per-column scale)
-// and only the pairs with p + q <= Lmax (Lmax <= 8) are formed.  Each digit
-// product is at most 2^10 and K <= 16384 per launch, so every tensor-core
-// sum S_pq = sum_k a_p z_q is an exact integer below 2^24 in the FP32
-// accumulator.  The epilogue converts S_pq to integers and accumulates
-// T = sum S_pq 2^(6(Lmax-p-q)) exactly in int64 (|T| < 2^62), then applies
-// R -= 2^(e_i + f_j - 6 Lmax) * T in FP64: the one rounding of the whole
+//     Z(k,j)  = 2^f_j * sum_{q=1..2} z_q(k,j) 2^(-8q),   |z_q| <= 128,
+// and only the pairs with 6p + 8q <= budget are formed: slices p = 1..P with
+// z_1, and p = 1..P2 also with z_2.  Each digit product is at most 2^12 and
+// the K range is accumulated in chunks of at most 4096, so every tensor-core
+// sum S_pq = sum_k a_p z_q of a chunk is an exact integer of at most 2^24 in
+// the FP32 accumulator.  The epilogue converts S_pq to integers and adds
+// S_pq 2^(W - 6p - 8q) into int64 sums T (W = the largest weight exponent
+// formed; with K <= 16384 per launch, |T| < 4 * 2^60.1 < 2^63), then
+// applies R -= 2^(e_i + f_j - W) T in FP64: the one rounding of the whole
 // product is that of T to FP64.
 //
-// One CTA per 128 x 128 tile of R.  Pass p (p = 1..Lmax-1) multiplies slice
-// a_p (128 x 64 per stage) with [z_1; z_2] (256 x 64 per stage, both slices
-// of the same 128 columns) into one of two 128 x 256 TMEM accumulators, so
-// that draining pass p overlaps the MMAs of pass p+1.  Warp 0: TMA, warp 1:
-// TMEM + MMA issue, warps 2-9: epilogue (warp w drains TMEM lanes
-// 32*(w%4).., column half (w-2)/4).
+// One CTA per 128 x 128 tile of R.  Pass p multiplies slice a_p (128 x 64 per
+// stage) with [z_1; z_2] (256 x 64 per stage, both slices of the same 128
+// columns) into one of two 128 x 256 TMEM accumulators, so that draining
+// pass p overlaps the MMAs of pass p+1.  Warp 0: TMA, warp 1: TMEM + MMA
+// issue, warps 2-9: epilogue (warp w drains TMEM lanes 32*(w%4).., column
+// half (w-2)/4).  CTAs are rasterised in groups of 8 row tiles.
 #include "common.cuh"
 #include "tc_common.cuh"
 
@@ -42,7 +44,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                    double *__restrict__ R, int64_t ldr, const int *__restrict__ e_row,
                    const int *__restrict__ f_col, const double *__restrict__ dg,
                    const __nv_bfloat16 *__restrict__ Zg, int64_t zslice, float *__restrict__ Yout, int k_lo,
-                   int k_hi, int Lmax, int nMt, int nNt, int *status)
+                   int k_hi, int P, int P2, int W, int nMt, int nNt, int *status)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -62,8 +64,12 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const int i0 = m_blk * BM, j0 = n_blk * BNO;
     const int k_end = min(k_hi, i0 + BM);
     if (k_end <= k_lo) return;  // tile entirely above the diagonal: nothing to add
-    const int nk = (k_end - k_lo) / BK;
-    const int P = Lmax - 1;     // slices a_1 .. a_{Lmax-1}
+    // exactness needs K <= 4096 per tensor-memory accumulation: the K range
+    // is cut into chunks of at most 4096, each pass of each chunk drained
+    // separately into the same int64 sums (|T| < 4 * 2^60.1 over 4 chunks)
+    constexpr int KC = 4096;
+    const int nchunks = (k_end - k_lo + KC - 1) / KC;
+    const int npass = nchunks * P;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -89,26 +95,30 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             tc::tma_prefetch_desc(&tmA);
             tc::tma_prefetch_desc(&tmZ);
             int g = 0;
-            for (int p = 0; p < P && !*ab; p++) {
-                for (int kt = 0; kt < nk; kt++, g++) {
+            for (int cp = 0; cp < npass && !*ab; cp++) {
+                const int c = cp / P, p = cp % P;
+                const int kc0 = k_lo + c * KC, kc1 = min(kc0 + KC, k_end);
+                for (int kk = kc0; kk < kc1; kk += BK, g++) {
                     const int s = g % STAGES;
                     const uint32_t ph = (g / STAGES) & 1;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) break;
                     tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                    tc::tma_load_3d(&tmA, &full[s], sA + s * A_BYTES, k_lo + kt * BK, i0, p);
-                    tc::tma_load_3d(&tmZ, &full[s], sB + s * B_BYTES, k_lo + kt * BK, j0, 0);
+                    tc::tma_load_3d(&tmA, &full[s], sA + s * A_BYTES, kk, i0, p);
+                    tc::tma_load_3d(&tmZ, &full[s], sB + s * B_BYTES, kk, j0, 0);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             int g = 0;
-            for (int p = 0; p < P; p++) {
-                const int buf = p & 1;
-                const uint32_t use = p >> 1;
+            for (int cp = 0; cp < npass; cp++) {
+                const int c = cp / P, p = cp % P;
+                const int nk = (min(k_lo + (c + 1) * KC, k_end) - (k_lo + c * KC)) / BK;
+                const int buf = cp & 1;
+                const uint32_t use = cp >> 1;
                 if (!tc::mbar_wait(&acce[buf], (use & 1) ^ 1, ab, status, tc::TC_TIMEOUT_MMA)) break;
                 tc::tc_fence_after();
-                const bool two = (p + 3) <= Lmax;  // pair (p+1, 2) still needed
+                const bool two = p < P2;  // pair (p+1, 2) formed
                 const uint32_t idesc = two ? tc::idesc_bf16_f32(BM, 256) : tc::idesc_bf16_f32(BM, 128);
                 const uint32_t d = tmem + uint32_t(buf * 256);
                 bool ok = true;
@@ -140,17 +150,18 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
         for (int c = 0; c < 64; c++) T[c] = 0;
         bool ok = true;
-        for (int p = 0; p < P; p++) {
-            const int buf = p & 1;
-            const uint32_t use = p >> 1;
+        for (int cp = 0; cp < npass; cp++) {
+            const int p = cp % P;
+            const int buf = cp & 1;
+            const uint32_t use = cp >> 1;
             if (!tc::mbar_wait(&accf[buf], use & 1, ab, status, tc::TC_TIMEOUT_EPILOGUE)) {
                 ok = false;
                 break;
             }
             tc::tc_fence_after();
-            const bool two = (p + 3) <= Lmax;
-            const int s1 = 6 * (Lmax - (p + 2));
-            const int s2 = 6 * (Lmax - (p + 3));
+            const bool two = p < P2;
+            const int s1 = W - (6 * (p + 1) + 8);
+            const int s2 = W - (6 * (p + 1) + 16);
             const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 256 + half * 64);
 #pragma unroll
             for (int c0 = 0; c0 < 64; c0 += 16) {
@@ -175,33 +186,33 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
         if (ok) {
             const int gi = i0 + row;
-            const int ei = e_row[gi] - 6 * Lmax;
+            const int ei = e_row[gi] - W;
             // the diagonal term Mv(i,i) Z(i,j), exactly in FP64, once: in
             // the launch whose K range holds column i
             const bool has_diag = gi >= k_lo && gi < k_hi;
             const double di = has_diag ? dg[gi] : 0.0;
-            // 4 columns at a time: every load is issued before the stores
+            // 2 columns at a time: every load is issued before the stores
 #pragma unroll
-            for (int c0 = 0; c0 < 64; c0 += 4) {
-                double rv[4];
-                int fj[4];
-                float zv[4];
+            for (int c0 = 0; c0 < 64; c0 += 2) {
+                double rv[2];
+                int fj[2];
+                float zv[2];
 #pragma unroll
-                for (int c = 0; c < 4; c++) {
+                for (int c = 0; c < 2; c++) {
                     const int gj = j0 + half * 64 + c0 + c;
                     rv[c] = R[gi + int64_t(gj) * ldr];
                     fj[c] = f_col[gj];
                     zv[c] = 0.f;
                     if (has_diag) {
                         const int64_t zo = int64_t(gj) * ldr + gi;
-                        zv[c] = __bfloat162float(Zg[zo]) * 64.0f + __bfloat162float(Zg[zslice + zo]);
+                        zv[c] = __bfloat162float(Zg[zo]) * 256.0f + __bfloat162float(Zg[zslice + zo]);
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < 4; c++) {
+                for (int c = 0; c < 2; c++) {
                     const int gj = j0 + half * 64 + c0 + c;
                     double sub = ldexp(static_cast<double>(T[c0 + c]), ei + fj[c]);
-                    if (has_diag) sub += di * ldexp(double(zv[c]), fj[c] - 12);
+                    if (has_diag) sub += di * ldexp(double(zv[c]), fj[c] - 16);
                     const double rn = rv[c] - sub;
                     R[gi + int64_t(gj) * ldr] = rn;
                     // the launch holding row i's diagonal is the last to touch
@@ -224,14 +235,17 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 // R (kp x np, FP64 column-major, ldr) -= Mv * Z over k in [k_lo, k_hi),
 // with A slices (7 x kp x kp BF16 row-major, contiguous) and Z slices
 // (2 x np x kp BF16: slice q holds column j of z_q at Zs + q*np*kp + j*kp).
-// kp, np multiples of 128; k_lo, k_hi multiples of 64; k_hi - k_lo <= 16384.
+// kp, np multiples of 128; k_lo, k_hi multiples of 64; k_hi - k_lo <= 16384;
+// P A slices with z_1, the first P2 of them also with z_2.
 int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
-                       const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int Lmax,
-                       cudaStream_t s, int *status)
+                       const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int P,
+                       int P2, cudaStream_t s, int *status)
 {
     if (kp <= 0 || np <= 0 || k_hi <= k_lo) return 0;
-    if (kp % 128 || np % 128 || k_lo % 64 || k_hi % 64 || k_hi - k_lo > 16384 || Lmax < 2 || Lmax > 8)
+    if (kp % 128 || np % 128 || k_lo % 64 || k_hi % 64 || k_hi - k_lo > 16384 || P < 1 || P > 7 || P2 < 0 ||
+        P2 > P)
         return GB_STATUS_CUDA_ERROR;
+    const int W = (P2 > 0 && 6 * P2 + 16 > 6 * P + 8) ? 6 * P2 + 16 : 6 * P + 8;
     if (kp > 0x7fffffffLL || np > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     CUtensorMap ta, tz;
     {
@@ -258,18 +272,19 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
     const int64_t nM = kp / BM, nN = np / BNO;
     if (nM > 65535 || nN > 65535 || nM * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     dim3 grid((unsigned)(nM * nN));
-    // algorithmic work: (Lmax-1) passes over the lower triangle of the K range
+    // algorithmic work: P passes (P2 of them two slices wide) over the lower
+    // triangle of the K range
     double tri = 0;
     for (int64_t i0 = 0; i0 < kp; i0 += BM) {
         int64_t ke = i0 + BM < k_hi ? i0 + BM : k_hi;
         if (ke > k_lo) tri += double(ke - k_lo);
     }
     double flops = 0;
-    for (int p = 0; p < Lmax - 1; p++) flops += 2.0 * BM * tri * np * ((p + 3 <= Lmax) ? 2 : 1);
+    for (int p = 0; p < P; p++) flops += 2.0 * BM * tri * np * (p < P2 ? 2 : 1);
     LaunchScope ls(KK_RESIDUAL, s, flops, 16.0 * kp * np);
     tc_residual_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(
         ta, tz, R, ldr, e_row, f_col, dg, static_cast<const __nv_bfloat16 *>(Zs), np * kp, Yout, (int)k_lo,
-        (int)k_hi, Lmax, (int)nM, (int)nN, st);
+        (int)k_hi, P, P2, W, (int)nM, (int)nN, st);
     return check(cudaGetLastError());
 }
 
