@@ -8,7 +8,12 @@
 // model (Section V-A, the TS(i) leaves) into a fully parallel product.
 //
 // Storage ("band"): block b occupies band[(b*128 + c)*128 + i] = L_b(i, c),
-// i.e. each block column-major with leading dimension 128.
+// i.e. each block column-major with leading dimension 128.  The inverses use
+// a packed "strip" layout in the same 128*128-float slot per block: strip g
+// (g = 0..31) holds rows 4g..4g+3 of L_b^-1 for the columns k = 0..4g+3 it can
+// be nonzero in, element (4g+j, k) at strip_off(g) + 4k + j.  That keeps the
+// lower triangle only (33 KB instead of 64 KB in shared memory) and gives
+// each thread's four rows of one column as one 16-byte vector.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include "common.cuh"
@@ -17,6 +22,28 @@ namespace gb {
 namespace {
 
 constexpr int NBI = 128;
+
+// Ampere-style asynchronous global -> shared copies (no register staging).
+__device__ __forceinline__ void cp_async16(float *dst, const float *src)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+// copies 4 bytes, or writes zero when `in` is false (source size 0)
+__device__ __forceinline__ void cp_async4_zfill(float *dst, const float *src, bool in)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    const int n = in ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+constexpr int NSTRIP = NBI / 4;
+constexpr int STRIP_FLOATS = 8 * NSTRIP * (NSTRIP + 1);  // 8448
+__host__ __device__ constexpr int strip_off(int g) { return 8 * g * (g + 1); }
 
 // One CTA (128 threads) per diagonal block: thread j forms column j of L^-1
 // by forward substitution on e_j (row form, FP32, two partial sums).
@@ -49,99 +76,155 @@ __global__ void __launch_bounds__(NBI) invert_blocks_kernel(const float *__restr
         X[i * (NBI + 1) + j] = v;
     }
     __syncthreads();
-    for (int idx = j; idx < NBI * NBI; idx += NBI) {
-        const int i = idx % NBI, c = idx / NBI;
-        Ib[idx] = X[i * (NBI + 1) + c];
+    // strip layout (the zeros above the diagonal inside each 4 x 4 diagonal
+    // piece are stored explicitly)
+    for (int g = 0; g < NSTRIP; g++) {
+        const int cnt = (4 * g + 4) * 4;
+        for (int e = j; e < cnt; e += NBI) Ib[strip_off(g) + e] = X[(4 * g + (e & 3)) * (NBI + 1) + (e >> 2)];
     }
 }
 
 // Y[b0:b0+nr, :] = Linv * Y[b0:b0+nr, :] for a block of nr <= 128 rows, in
 // place (each CTA reads its whole 128 x 64 column panel before writing it),
-// plus the BF16 copy.  256 threads, each an 8 x 4 register tile: rows
-// ty*4 .. +3 and 64 + ty*4 .. +3, columns tx*4 .. +3.
-constexpr int AC = 64;  // columns per CTA
-// FP8 = true: instead of the BF16 copy, an FP8 (E4M3) copy Y8 with one
-// power-of-two scale for the CTA's 128 x 64 block (written to *s8 + blockIdx.x).
+// plus the BF16 (or FP8) copy.  256 threads over a 128 x 64 panel; thread
+// (tx, ty) = (tid % 16, tid / 16) owns the columns tx, tx+16, tx+32, tx+48
+// and the eight rows 4ty .. 4ty+3 and 124-4ty .. 127-4ty.  Pairing a low and
+// a high row group makes every thread's share of the triangle the same: rows
+// 4ty.. need k < 4ty+4 and rows 124-4ty.. need k < 128-4ty, so each thread
+// does 2112 FMAs, and the two row-group pairs of one warp differ by only
+// four iterations.  The panel keeps Y's column-major layout in shared memory
+// with an odd column stride: staging stores and operand reads are free of
+// bank conflicts (the 16 column owners of a warp hit 16 distinct banks; the
+// two row groups share each address).  Results go straight from registers
+// to global memory.
+constexpr int AC = 64;
+constexpr int LDC = NBI + 1;  // shared column stride of the panel
+// FP8 = true: instead of the BF16 copy, an FP8 (E4M3) copy
+// Y8 with one power-of-two scale for the CTA's 128 x 64 block (written to
+// s8[blockIdx.x]).
 template <bool FP8>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(4 * AC)
 apply_inverse_kernel(const float *__restrict__ Linv, float *__restrict__ Y, int64_t ldy,
                      __nv_bfloat16 *__restrict__ Ybf, int nr, int64_t ncols, uint8_t *__restrict__ Y8,
                      float *__restrict__ s8)
 {
     extern __shared__ __align__(16) float sm[];
-    float *Ls = sm;                 // Ls[k*NBI + i] = Linv(i, k)   (column k contiguous)
-    float *Ys = sm + NBI * NBI;     // Ys[k*(AC+4) + c]            (row k contiguous)
-    constexpr int LDY = AC + 4;
+    float *Ls = sm;                 // strips of Linv
+    float *Ys = sm + STRIP_FLOATS;  // Ys[c*LDC + i]   (column c contiguous)
+    constexpr int nthr = 4 * AC;
     const int tid = threadIdx.x;
     const int64_t c0 = int64_t(blockIdx.x) * AC;
-    for (int idx = tid; idx < NBI * NBI / 4; idx += 256)
-        reinterpret_cast<float4 *>(Ls)[idx] = reinterpret_cast<const float4 *>(Linv)[idx];
-    for (int idx = tid; idx < NBI * AC; idx += 256) {
-        const int i = idx % NBI, c = idx / NBI;  // Y column-major: contiguous along i
-        float v = 0.f;
-        if (i < nr && c0 + c < ncols) v = Y[i + (c0 + c) * ldy];
-        Ys[i * LDY + c] = v;
+    // all staging loads go out as asynchronous copies before the one wait
+    for (int idx = tid; idx < STRIP_FLOATS / 4; idx += nthr) cp_async16(Ls + 4 * idx, Linv + 4 * idx);
+    // 128 * AC = 32 * nthr elements; consecutive threads take consecutive rows
+#pragma unroll 8
+    for (int it = 0; it < 32; it++) {
+        const int idx = tid + it * nthr;
+        const int i = idx & (NBI - 1), c = idx >> 7;
+        const bool in = i < nr && c0 + c < ncols;
+        cp_async4_zfill(Ys + c * LDC + i, in ? Y + i + (c0 + c) * ldy : Y, in);
     }
+    cp_async_wait_all();
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;
-    const int r0 = ty * 4, r1 = 64 + ty * 4, cc = tx * 4;
+    const int rlo = 4 * ty, rhi = NBI - 4 - 4 * ty;
+    const float *S0 = Ls + strip_off(ty);
+    const float *S1 = Ls + strip_off(NSTRIP - 1 - ty);
+    const float *yb = Ys + tx * LDC;  // column tx + 16c at yb + 16c*LDC
     float acc[8][4];
 #pragma unroll
     for (int r = 0; r < 8; r++)
 #pragma unroll
         for (int c = 0; c < 4; c++) acc[r][c] = 0.f;
-    // Linv is lower triangular: rows < 64 need k <= r0+3, rows >= 64 need all k <= r1+3
-    const int kend_hi = r1 + 4;
-    for (int k = 0; k < kend_hi; k++) {
-        const float4 a0 = *reinterpret_cast<const float4 *>(&Ls[k * NBI + r0]);
-        const float4 a1 = *reinterpret_cast<const float4 *>(&Ls[k * NBI + r1]);
-        const float4 b = *reinterpret_cast<const float4 *>(&Ys[k * LDY + cc]);
+    int k = 0;
+#pragma unroll 2
+    for (; k < rlo + 4; k++) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(S0 + 4 * k);
+        const float4 a1 = *reinterpret_cast<const float4 *>(S1 + 4 * k);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bv[4] = {b.x, b.y, b.z, b.w};
+        float bv[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) bv[c] = yb[16 * c * LDC + k];
 #pragma unroll
         for (int r = 0; r < 8; r++)
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
     }
-    __syncthreads();
-    // results back through shared memory for coalesced column-major stores
+#pragma unroll 4
+    for (; k < rhi + 4; k++) {
+        const float4 a1 = *reinterpret_cast<const float4 *>(S1 + 4 * k);
+        const float av[4] = {a1.x, a1.y, a1.z, a1.w};
+        float bv[4];
 #pragma unroll
-    for (int r = 0; r < 8; r++) {
-        const int i = r < 4 ? r0 + r : r1 + (r - 4);
+        for (int c = 0; c < 4; c++) bv[c] = yb[16 * c * LDC + k];
 #pragma unroll
-        for (int c = 0; c < 4; c++) Ys[i * LDY + cc + c] = acc[r][c];
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[4 + r][c] = fmaf(av[r], bv[c], acc[4 + r][c]);
     }
-    __syncthreads();
     float scale_inv = 1.f;
     if (FP8) {
         // block maximum -> power-of-two scale s with amax / s <= 448
-        __shared__ float red[8];
+        __shared__ float red[nthr / 32];
         float mx = 0.f;
-        for (int idx = tid; idx < NBI * AC; idx += 256) mx = fmaxf(mx, fabsf(Ys[(idx % NBI) * LDY + idx / NBI]));
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if ((h ? rhi : rlo) + r < nr && c0 + tx + 16 * c < ncols)
+                        mx = fmaxf(mx, fabsf(acc[4 * h + r][c]));
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if ((tid & 31) == 0) red[tid >> 5] = mx;
         __syncthreads();
         mx = 0.f;
-        for (int w = 0; w < 8; w++) mx = fmaxf(mx, red[w]);
+        for (int w = 0; w < nthr / 32; w++) mx = fmaxf(mx, red[w]);
         const float sc = mx > 0.f ? exp2f(ceilf(log2f(mx / 448.f))) : 1.f;
         scale_inv = 1.f / sc;
         if (tid == 0) s8[blockIdx.x] = sc;
     }
-    for (int idx = tid; idx < NBI * AC; idx += 256) {
-        const int i = idx % NBI, c = idx / NBI;
-        if (i < nr && c0 + c < ncols) {
-            const float v = Ys[i * LDY + c];
-            Y[i + (c0 + c) * ldy] = v;
-            if (FP8)
-                Y8[i + (c0 + c) * ldy] = __nv_cvt_float_to_fp8(v * scale_inv, __NV_SATFINITE, __NV_E4M3);
-            else
-                Ybf[i + (c0 + c) * ldy] = __float2bfloat16_rn(v);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const int64_t col = c0 + tx + 16 * c;
+        if (col >= ncols) continue;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int r0 = h ? rhi : rlo;
+            const float *a = acc[4 * h];
+            const float v0 = a[0 * 4 + c], v1 = a[1 * 4 + c], v2 = a[2 * 4 + c], v3 = a[3 * 4 + c];
+            const int64_t o = r0 + col * ldy;
+            if (r0 + 3 < nr) {
+                *reinterpret_cast<float4 *>(&Y[o]) = make_float4(v0, v1, v2, v3);
+                if (FP8) {
+                    const uint32_t q0 = __nv_cvt_float_to_fp8(v0 * scale_inv, __NV_SATFINITE, __NV_E4M3);
+                    const uint32_t q1 = __nv_cvt_float_to_fp8(v1 * scale_inv, __NV_SATFINITE, __NV_E4M3);
+                    const uint32_t q2 = __nv_cvt_float_to_fp8(v2 * scale_inv, __NV_SATFINITE, __NV_E4M3);
+                    const uint32_t q3 = __nv_cvt_float_to_fp8(v3 * scale_inv, __NV_SATFINITE, __NV_E4M3);
+                    *reinterpret_cast<uint32_t *>(&Y8[o]) = q0 | (q1 << 8) | (q2 << 16) | (q3 << 24);
+                } else {
+                    __nv_bfloat162 p0 = __floats2bfloat162_rn(v0, v1), p1 = __floats2bfloat162_rn(v2, v3);
+                    uint2 w;
+                    w.x = *reinterpret_cast<uint32_t *>(&p0);
+                    w.y = *reinterpret_cast<uint32_t *>(&p1);
+                    *reinterpret_cast<uint2 *>(&Ybf[o]) = w;
+                }
+            } else {
+                const float vv[4] = {v0, v1, v2, v3};
+#pragma unroll
+                for (int r = 0; r < 4; r++)
+                    if (r0 + r < nr) {
+                        Y[o + r] = vv[r];
+                        if (FP8) Y8[o + r] = __nv_cvt_float_to_fp8(vv[r] * scale_inv, __NV_SATFINITE, __NV_E4M3);
+                        else Ybf[o + r] = __float2bfloat16_rn(vv[r]);
+                    }
+            }
         }
     }
 }
 
 constexpr size_t INV_SMEM = size_t(NBI) * NBI * 4 + size_t(NBI) * (NBI + 1) * 4;
-constexpr size_t APPLY_SMEM = size_t(NBI) * NBI * 4 + size_t(NBI) * (AC + 4) * 4;
+constexpr size_t apply_smem(int ac) { return size_t(STRIP_FLOATS) * 4 + size_t(ac) * LDC * 4; }
 
 }  // namespace
 
@@ -152,9 +235,9 @@ int diag_inv_prepare()
         GB_CUDA(cudaFuncSetAttribute(invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)INV_SMEM));
         GB_CUDA(cudaFuncSetAttribute(apply_inverse_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)APPLY_SMEM));
+                                     (int)apply_smem(AC)));
         GB_CUDA(cudaFuncSetAttribute(apply_inverse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)APPLY_SMEM));
+                                     (int)apply_smem(AC)));
         done = true;
     }
     return 0;
@@ -177,10 +260,12 @@ int launch_apply_inverse(const float *Linv_b, float *Yb, int64_t ldy, __nv_bfloa
     if (nr <= 0 || ncols <= 0) return 0;
     if (nr > NBI) return GB_STATUS_CUDA_ERROR;
     GB_TRY(diag_inv_prepare());
+    if (ldy % 4 || (reinterpret_cast<uintptr_t>(Yb) & 15) || (reinterpret_cast<uintptr_t>(Ybf_b) & 7))
+        return GB_STATUS_CUDA_ERROR;
     const int64_t grid = (ncols + AC - 1) / AC;
     LaunchScope ls(KK_DIAG, s, double(nr) * nr * ncols, 4.0 * (double(nr) * nr + 2.0 * nr * ncols) + 2.0 * nr * ncols);
-    apply_inverse_kernel<false><<<(unsigned)grid, 256, APPLY_SMEM, s>>>(Linv_b, Yb, ldy, Ybf_b, nr, ncols,
-                                                                         nullptr, nullptr);
+    apply_inverse_kernel<false><<<(unsigned)grid, 4 * AC, apply_smem(AC), s>>>(Linv_b, Yb, ldy, Ybf_b, nr, ncols,
+                                                                                nullptr, nullptr);
     return check(cudaGetLastError());
 }
 
@@ -192,10 +277,12 @@ int launch_apply_inverse_fp8(const float *Linv_b, float *Yb, int64_t ldy, uint8_
     if (nr <= 0 || ncols <= 0) return 0;
     if (nr > NBI) return GB_STATUS_CUDA_ERROR;
     GB_TRY(diag_inv_prepare());
+    if (ldy % 4 || (reinterpret_cast<uintptr_t>(Yb) & 15) || (reinterpret_cast<uintptr_t>(Y8_b) & 3))
+        return GB_STATUS_CUDA_ERROR;
     const int64_t grid = (ncols + AC - 1) / AC;
     LaunchScope ls(KK_DIAG, s, double(nr) * nr * ncols, 4.0 * (double(nr) * nr + 2.0 * nr * ncols) + 1.0 * nr * ncols);
-    apply_inverse_kernel<true><<<(unsigned)grid, 256, APPLY_SMEM, s>>>(Linv_b, Yb, ldy, nullptr, nr, ncols, Y8_b,
-                                                                        s8_b);
+    apply_inverse_kernel<true><<<(unsigned)grid, 4 * AC, apply_smem(AC), s>>>(Linv_b, Yb, ldy, nullptr, nr, ncols,
+                                                                               Y8_b, s8_b);
     return check(cudaGetLastError());
 }
 

@@ -89,15 +89,17 @@ struct TileCfg {
     static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 8 ? 8 : (192 * 1024) / STAGE_BYTES;
     static constexpr size_t SMEM_BYTES = 1024 + STAGES * size_t(STAGE_BYTES) + 256;
+    // a short K needs fewer stages; the smaller footprint lets several CTAs
+    // share an SM (thin updates are latency-bound)
+    static size_t smem_for(int nst) { return 1024 + nst * size_t(STAGE_BYTES) + 256; }
 };
 
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     float *__restrict__ C, int64_t ldc, int M, int N, int K, float alpha, int nMt, int nNt,
-                    int *status)
+                    int STAGES, int *status)
 {
-    constexpr int STAGES = TileCfg<BN>::STAGES;
     constexpr uint32_t B_BYTES = TileCfg<BN>::B_BYTES;
     constexpr uint32_t STAGE_BYTES = TileCfg<BN>::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
@@ -168,7 +170,31 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         const int q = warp & 3;
         const int row = q * 32 + lane;
         const int64_t gi = int64_t(m_blk) * BM + row;
-        if (tc::mbar_wait(accf, 0, ab, status, tc::TC_TIMEOUT_EPILOGUE)) {
+        if constexpr (BN <= 64) {
+            // narrow tiles serve thin updates (small K): the C tile is read
+            // while the loads and MMAs run
+            float cp[BN];
+            const int64_t gj0 = int64_t(n_blk) * BN;
+            if (gi < M) {
+#pragma unroll
+                for (int j = 0; j < BN; j++) cp[j] = (gj0 + j < N) ? C[gi + (gj0 + j) * ldc] : 0.f;
+            }
+            if (tc::mbar_wait(accf, 0, ab, status, tc::TC_TIMEOUT_EPILOGUE)) {
+                tc::tc_fence_after();
+#pragma unroll
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c0), r);
+                    tc::tmem_ld_wait();
+                    if (gi < M) {
+#pragma unroll
+                        for (int j = 0; j < 32; j++)
+                            if (gj0 + c0 + j < N)
+                                C[gi + (gj0 + c0 + j) * ldc] = alpha * cp[c0 + j] - __uint_as_float(r[j]);
+                    }
+                }
+            }
+        } else if (tc::mbar_wait(accf, 0, ab, status, tc::TC_TIMEOUT_EPILOGUE)) {
             tc::tc_fence_after();
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -197,6 +223,151 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     }
 }
 
+// Persistent form for wide updates: one CTA per SM walks the 128 x 256 tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... (grouped rasterisation) with
+// two TMEM accumulators (2 x 256 columns), so that the epilogue of one tile
+// runs while the MMAs of the next accumulate into the other buffer.  The TMA
+// ring runs continuously across tiles.  320 threads: warp 0 TMA, warp 1 MMA,
+// warps 2-9 epilogue (warps w and w+4 share TMEM lane quadrant w % 4 and
+// take one half of the tile's columns each).
+constexpr int PBN = 256, PSTAGES = 4;
+constexpr uint32_t P_B_BYTES = PBN * BK * 2, P_STAGE_BYTES = A_BYTES + P_B_BYTES;
+constexpr size_t P_SMEM_BYTES = 1024 + PSTAGES * size_t(P_STAGE_BYTES) + 256;
+
+__global__ void __launch_bounds__(320, 1)
+tc_gemm_bf16_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                               float *__restrict__ C, int64_t ldc, int M, int N, int K, float alpha, int nMt,
+                               int nNt, int *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + PSTAGES * A_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + PSTAGES * P_B_BYTES);
+    uint64_t *empty = full + PSTAGES;
+    uint64_t *tfull = empty + PSTAGES;  // [2] accumulator ready
+    uint64_t *tempty = tfull + 2;       // [2] accumulator drained
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = K / BK;
+    const int ntiles = nMt * nNt;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PSTAGES; s++) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&tfull[b], 1);
+            tc::mbar_init(&tempty[b], 8);  // one arrival per epilogue warp
+        }
+        abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, 2 * PBN);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    volatile int *ab = &abort_flag;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::tma_prefetch_desc(&tmA);
+            tc::tma_prefetch_desc(&tmB);
+            uint32_t kg = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                int m_blk, n_blk;
+                tc::raster_grouped(t, nMt, nNt, 8, m_blk, n_blk);
+                bool ok = true;
+                for (int kt = 0; kt < nk; kt++, kg++) {
+                    const int s = kg % PSTAGES;
+                    const uint32_t ph = (kg / PSTAGES) & 1;
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_arrive_expect_tx(&full[s], P_STAGE_BYTES);
+                    tc::tma_load_2d(&tmA, &full[s], sA + s * A_BYTES, kt * BK, m_blk * BM);
+                    tc::tma_load_2d(&tmB, &full[s], sB + s * P_B_BYTES, kt * BK, n_blk * PBN);
+                }
+                if (!ok) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, PBN);
+            uint32_t kg = 0;
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, it++) {
+                const int buf = it & 1;
+                const uint32_t use = uint32_t(it >> 1);
+                if (!tc::mbar_wait(&tempty[buf], (use & 1) ^ 1, ab, status, tc::TC_TIMEOUT_MMA)) break;
+                tc::tc_fence_after();
+                const uint32_t d = tmem + uint32_t(buf * PBN);
+                for (int kt = 0; kt < nk; kt++, kg++) {
+                    const int s = kg % PSTAGES;
+                    const uint32_t ph = (kg / PSTAGES) & 1;
+                    if (!tc::mbar_wait(&full[s], ph, ab, status, tc::TC_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
+                    const uint32_t b0 = tc::smem_u32(sB + s * P_B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++)
+                        tc::mma_f16(d, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
+                                    idesc, (kt | kk) != 0);
+                    tc::mma_commit(&empty[s]);
+                }
+                if (ok) tc::mma_commit(&tfull[buf]);
+            }
+        }
+    } else {
+        const int q = warp & 3;                 // TMEM lane quadrant of this warp
+        const int half = (warp - 2) >> 2;       // which 128 columns of the tile
+        const int row = q * 32 + lane;
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+            int m_blk, n_blk;
+            tc::raster_grouped(t, nMt, nNt, 8, m_blk, n_blk);
+            const int buf = it & 1;
+            const uint32_t use = uint32_t(it >> 1);
+            if (!tc::mbar_wait(&tfull[buf], use & 1, ab, status, tc::TC_TIMEOUT_EPILOGUE)) break;
+            tc::tc_fence_after();
+            const int64_t gi = int64_t(m_blk) * BM + row;
+#pragma unroll 1
+            for (int c0 = half * (PBN / 2); c0 < (half + 1) * (PBN / 2); c0 += 32) {
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * PBN + c0), r);
+                tc::tmem_ld_wait();
+                if (gi < M) {
+                    float cv[32];
+                    const int64_t gj0 = int64_t(n_blk) * PBN + c0;
+#pragma unroll
+                    for (int j = 0; j < 32; j++) cv[j] = (gj0 + j < N) ? C[gi + (gj0 + j) * ldc] : 0.f;
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        if (gj0 + j < N) C[gi + (gj0 + j) * ldc] = alpha * cv[j] - __uint_as_float(r[j]);
+                }
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[buf]);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 2 * PBN);
+    }
+}
+
 }  // namespace
 
 template <int BN>
@@ -213,8 +384,30 @@ static int prepare_bn()
 
 // One-time per-process set-up (kernel attributes, device status word); must
 // run before any stream capture that launches the kernel.
+static int prepare_persistent()
+{
+    static bool attr = false;
+    if (!attr) {
+        GB_CUDA(cudaFuncSetAttribute(tc_gemm_bf16_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)P_SMEM_BYTES));
+        attr = true;
+    }
+    return 0;
+}
+
+static int num_sms()
+{
+    static int n[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!n[dev] && cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n[dev];
+}
+
 int tc_gemm_prepare()
 {
+    GB_TRY(prepare_persistent());
+    if (num_sms() <= 0) return GB_STATUS_CUDA_ERROR;
     GB_TRY(prepare_bn<256>());
     GB_TRY(prepare_bn<128>());
     GB_TRY(prepare_bn<64>());
@@ -245,9 +438,41 @@ static int launch_bn(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda
     const int64_t nM = (M + BM - 1) / BM, nN = (N + BN - 1) / BN;
     if (nM > 65535 || nN > 65535 || nM * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     dim3 grid((unsigned)(nM * nN));
+    const int nk = int(K / BK);
+    const int nst = nk < TileCfg<BN>::STAGES ? nk : TileCfg<BN>::STAGES;
     LaunchScope ls(KK_GEMM_TC, s, 2.0 * M * N * K, 2.0 * (double(M) * K + double(K) * N) + 8.0 * M * N);
-    tc_gemm_bf16_kernel<BN><<<grid, 192, TileCfg<BN>::SMEM_BYTES, s>>>(ta, tb, C, ldc, (int)M, (int)N, (int)K,
-                                                                       alpha, (int)nM, (int)nN, st);
+    tc_gemm_bf16_kernel<BN><<<grid, 192, TileCfg<BN>::smem_for(nst), s>>>(ta, tb, C, ldc, (int)M, (int)N, (int)K,
+                                                                          alpha, (int)nM, (int)nN, nst, st);
+    return check(cudaGetLastError());
+}
+
+static int launch_persistent(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
+                             int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s, int *status)
+{
+    CUtensorMap ta, tb;
+    {
+        uint64_t dims[2] = {uint64_t(K), uint64_t(M)};
+        uint64_t strides[1] = {uint64_t(lda) * 2};
+        uint32_t box[2] = {BK, BM};
+        GB_TRY(encode_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, strides, box));
+    }
+    {
+        uint64_t dims[2] = {uint64_t(K), uint64_t(N)};
+        uint64_t strides[1] = {uint64_t(ldb) * 2};
+        uint32_t box[2] = {BK, uint32_t(PBN)};
+        GB_TRY(encode_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, strides, box));
+    }
+    GB_TRY(prepare_persistent());
+    int *st = status ? status : device_status_word();
+    if (!st) return GB_STATUS_CUDA_ERROR;
+    const int sms = num_sms();
+    if (sms <= 0) return GB_STATUS_CUDA_ERROR;
+    const int64_t nM = (M + BM - 1) / BM, nN = (N + PBN - 1) / PBN;
+    if (nM * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
+    const int64_t grid = nM * nN < sms ? nM * nN : sms;
+    LaunchScope ls(KK_GEMM_TC, s, 2.0 * M * N * K, 2.0 * (double(M) * K + double(K) * N) + 8.0 * M * N);
+    tc_gemm_bf16_persistent_kernel<<<(unsigned)grid, 320, P_SMEM_BYTES, s>>>(ta, tb, C, ldc, (int)M, (int)N, (int)K,
+                                                                            alpha, (int)nM, (int)nN, st);
     return check(cudaGetLastError());
 }
 
@@ -268,7 +493,7 @@ int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t 
     if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     const int64_t mt = (M + BM - 1) / BM;
     if (mt * ((N + 255) / 256) >= 2 * 152)
-        return launch_bn<256>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
+        return launch_persistent(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
     if (mt * ((N + 127) / 128) >= 2 * 152)
         return launch_bn<128>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
     return launch_bn<64>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
