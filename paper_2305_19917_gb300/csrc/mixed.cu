@@ -34,7 +34,7 @@ namespace gb {
 int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
                         int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s, int *status);
 int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
-                       const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int P,
+                       float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int P,
                        int P2, cudaStream_t s, int *status);
 int tc_gemm_prepare();
 int tc_gemm_fp8_prepare();
@@ -292,7 +292,7 @@ writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t
 // largest column ratio max|D~| / max|X| goes to norms[2] (as bits).
 __global__ void __launch_bounds__(256)
 slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bfloat16 *Zs, int *f_col,
-                  double *X, float *xmax, double *norms, int first)
+                  double *X, float *xmax, double *norms, int first, double *R, const double *dg)
 {
     const int64_t j = blockIdx.x;
     const float *y = Y + j * kp;
@@ -312,6 +312,7 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
     __nv_bfloat16 *z1 = Zs + j * kp;
     __nv_bfloat16 *z2 = Zs + np * kp + j * kp;
     double *x = X + j * kp;
+    double *r = R + j * kp;
     float sd = 0.f, sx = 0.f;
     for (int64_t i = threadIdx.x; i < kp; i += 256) {
         const int N = (be > 0) ? __float2int_rn(y[i] * up) : 0;
@@ -320,8 +321,12 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
         z1[i] = __int2bfloat16_rn(q1);
         z2[i] = __int2bfloat16_rn(q2);
         const float d = float(N) * down;  // exact
-        if (first) x[i] = double(d);
-        else x[i] += double(d);
+        const double dd = double(d);
+        if (first) x[i] = dd;
+        else x[i] += dd;
+        // the diagonal part of the residual update, R -= Mv(i,i) D(i,j), in
+        // FP64 (the strictly lower part follows on the tensor cores)
+        r[i] = fma(-dg[i], dd, r[i]);
         sd = fmaf(d, d, sd);
     }
     if (first) sx = sd;
@@ -453,12 +458,12 @@ void pairs_for(double rho, double tol, int *P, int *P2)
 // inside, chunks of 4096 keep every tensor-core sum exact (|a| <= 32,
 // |z| <= 128: 4096 * 32 * 128 = 2^24).
 int residual_update(double *R, const __nv_bfloat16 *As, const __nv_bfloat16 *Zs, const int *e_row, const int *f_col,
-                    const double *dg, float *Y, int64_t kp, int64_t np, int P, int P2, cudaStream_t s,
+                    float *Y, int64_t kp, int64_t np, int P, int P2, cudaStream_t s,
                     int *status_word)
 {
     for (int64_t lo = 0; lo < kp; lo += 16384) {
         int64_t hi = lo + 16384 < kp ? lo + 16384 : kp;
-        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, dg, Y, kp, np, lo, hi, P, P2, s, status_word));
+        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, Y, kp, np, lo, hi, P, P2, s, status_word));
     }
     return 0;
 }
@@ -665,7 +670,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
             {
                 LaunchScope ls(KK_CONVERT, s, 0, 20.0 * double(nel));
                 slice_cols_kernel<<<(unsigned)np, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms,
-                                                                t == 0);
+                                                                t == 0, R, dg);
                 if ((st = check(cudaGetLastError()))) break;
             }
             if ((st = check(cudaMemcpyAsync(h_norm, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)))) break;
@@ -697,7 +702,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
             int P = 7, P2 = 6;
             pairs_for(t == 0 ? 1.0 : h_norm[2], tol, &P, &P2);
             Lmax = P * 10 + P2;  // recorded in the history as 10*P + P2
-            if ((st = residual_update(R, As, Zs, e_row, f_col, dg, Y, kp, np, P, P2, s, status_word))) break;
+            if ((st = residual_update(R, As, Zs, e_row, f_col, Y, kp, np, P, P2, s, status_word))) break;
         }
         if (st) break;
         {

@@ -5,7 +5,8 @@
 // where both factors are given as fixed-point digit slices (BF16 holding
 // small integers), the strictly lower part of Mv as
 //     Mv(i,k) = 2^e_i * sum_{p=1..7} a_p(i,k) 2^(-6p),   |a_p| <= 32
-// (the diagonal Mv(i,i) is applied separately, in FP64), and
+// (the diagonal part R -= Mv(i,i) Z(i,j) is applied in FP64 where the
+// correction digits are formed, outside this kernel), and
 //     Z(k,j)  = 2^f_j * sum_{q=1..2} z_q(k,j) 2^(-8q),   |z_q| <= 128,
 // and only the pairs with 6p + 8q <= budget are formed: slices p = 1..P with
 // z_1, and p = 1..P2 also with z_2.  Each digit product is at most 2^12 and
@@ -17,12 +18,21 @@
 // applies R -= 2^(e_i + f_j - W) T in FP64: the one rounding of the whole
 // product is that of T to FP64.
 //
-// One CTA per 128 x 128 tile of R.  Pass p multiplies slice a_p (128 x 64 per
-// stage) with [z_1; z_2] (256 x 64 per stage, both slices of the same 128
-// columns) into one of two 128 x 256 TMEM accumulators, so that draining
-// pass p overlaps the MMAs of pass p+1.  Warp 0: TMA, warp 1: TMEM + MMA
-// issue, warps 2-9: epilogue (warp w drains TMEM lanes 32*(w%4).., column
-// half (w-2)/4).  CTAs are rasterised in groups of 8 row tiles.
+// One CTA per 128 x 128 tile of R; the CTAs run in clusters of two that
+// hold vertically adjacent row tiles of the same columns, so both need the
+// same correction digits: each CTA loads one 64-column half of every Z tile
+// and multicasts it to both (L2 reads per CTA and K step: 16 KB of A plus
+// 16 or 8 KB of Z instead of 16 + 32).  Pass p multiplies slice a_p
+// (128 x 64 per stage) with [z_1; z_2] (256 x 64, both slices of the same
+// 128 columns; z_2 only in passes p < P2) into one of two 128 x 256 TMEM
+// accumulators, so that draining pass p overlaps the MMAs of pass p+1.
+// Both CTAs of a pair step through the same K range (the longer of the
+// two); the upper tile issues no MMAs for the K steps above its diagonal.
+// A stage is refilled only after both CTAs' MMAs released it (each MMA
+// commit arrives on the stage's empty barrier in both CTAs).  Warp 0: TMA,
+// warp 1: TMEM + MMA issue, warps 2-9: epilogue (warp w drains TMEM lanes
+// 32*(w%4).., column half (w-2)/4).  Pairs are rasterised in groups of 4
+// (8 row tiles).
 #include "common.cuh"
 #include "tc_common.cuh"
 
@@ -34,17 +44,71 @@ namespace {
 
 constexpr int BM = 128, BNO = 128, BK = 64, STAGES = 4;
 constexpr uint32_t A_BYTES = BM * BK * 2;          // one A slice tile
-constexpr uint32_t B_BYTES = 2 * BNO * BK * 2;     // z_1 and z_2 tiles
+constexpr uint32_t ZS_BYTES = BNO * BK * 2;        // one Z slice tile (128 columns)
+constexpr uint32_t B_BYTES = 2 * ZS_BYTES;         // z_1 and z_2 tiles
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr size_t SMEM_BYTES = 1024 + STAGES * size_t(STAGE_BYTES) + 256;
 constexpr int NTHREADS = 320;
+constexpr uint16_t kPair = 0x3;
+static_assert(BM * BNO * 8 <= STAGES * STAGE_BYTES, "final staging fits the ring");
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+// The FP64 pipe of an sm_103 SM retires two operations per clock, so the
+// final update builds its doubles with integer operations instead of
+// conversions and ldexp:
+// T * 2^e rounded to the nearest double (ties to even), i.e. the value of
+// ldexp((double)T, e), for |T| < 2^63.  Results outside the normal exponent
+// range take the library path.
+__device__ __forceinline__ double scaled_i64_to_f64(long long T, int e)
+{
+    if (T == 0) return 0.0;
+    const unsigned long long sign = T < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long u = T < 0 ? 0ull - static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T);
+    const int lz = __clzll(static_cast<long long>(u));
+    int msb = 63 - lz;
+    const unsigned long long m = u << lz;  // leading one at bit 63
+    unsigned long long keep = m >> 11;     // 53 significant bits
+    const unsigned long long rem = m & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (keep & 1ull))) keep++;
+    if (keep >> 53) {  // rounded up to the next power of two
+        keep >>= 1;
+        msb++;
+    }
+    const int ex = msb + e;
+    if (ex < -1022 || ex > 1023) return ldexp(static_cast<double>(T), e);
+    return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(ex + 1023) << 52) |
+                                                       (keep & ((1ull << 52) - 1))));
+}
+// x rounded to the nearest float (ties to even), as __double2float_rn(x);
+// zero, subnormal, overflowing and non-finite inputs take the library path.
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int ex = int((b >> 52) & 0x7FF) - 1023;
+    if (ex < -126 || ex > 127) return __double2float_rn(x);
+    const unsigned long long mant = b & ((1ull << 52) - 1);
+    unsigned int keep = static_cast<unsigned int>(mant >> 29);
+    const unsigned long long rem = mant & ((1ull << 29) - 1);
+    if (rem > (1ull << 28) || (rem == (1ull << 28) && (keep & 1u))) keep++;
+    // a carry out of the mantissa moves into the exponent field, as it must
+    const unsigned int fb = static_cast<unsigned int>((b >> 32) & 0x80000000ull) |
+                            (static_cast<unsigned int>(ex + 127) << 23);
+    return __uint_as_float(fb + keep);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ,
                    double *__restrict__ R, int64_t ldr, const int *__restrict__ e_row,
-                   const int *__restrict__ f_col, const double *__restrict__ dg,
-                   const __nv_bfloat16 *__restrict__ Zg, int64_t zslice, float *__restrict__ Yout, int k_lo,
-                   int k_hi, int P, int P2, int W, int nMt, int nNt, int *status)
+                   const int *__restrict__ f_col, float *__restrict__ Yout, int k_lo,
+                   int k_hi, int P, int P2, int W, int nMt, int nMp, int nNt, int *status)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -56,14 +120,21 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint64_t *acce = accf + 2;        // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + 2);
     __shared__ int abort_flag;
+    __shared__ __align__(16) int fs[BNO];  // f_col of the tile's columns (final update)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int mg, n_blk;
-    tc::raster_grouped(int(blockIdx.x), nMt, nNt, 8, mg, n_blk);
-    const int m_blk = nMt - 1 - mg;  // longest K ranges first
-    const int i0 = m_blk * BM, j0 = n_blk * BNO;
-    const int k_end = min(k_hi, i0 + BM);
-    if (k_end <= k_lo) return;  // tile entirely above the diagonal: nothing to add
+    const int rank = int(tc::cluster_ctarank());
+    int pg, n_blk;
+    tc::raster_grouped(int(blockIdx.x >> 1), nMp, nNt, 4, pg, n_blk);
+    // longest K ranges first; rank 0 holds the lower tile of the pair, rank
+    // 1 the one above it (absent when nMt is odd and this is the top pair)
+    const int m0 = nMt - 1 - 2 * pg;
+    const int m_blk = m0 - rank;
+    const bool ghost = m_blk < 0;
+    const int i0 = ghost ? 0 : m_blk * BM, j0 = n_blk * BNO;
+    const int k_end = min(k_hi, m0 * BM + BM);                 // the pair's K range
+    const int k_own = ghost ? k_lo : min(k_hi, i0 + BM);       // this tile's
+    if (k_end <= k_lo) return;  // both tiles entirely above the diagonal
     // exactness needs K <= 4096 per tensor-memory accumulation: the K range
     // is cut into chunks of at most 4096, each pass of each chunk drained
     // separately into the same int64 sums (|T| < 4 * 2^60.1 over 4 chunks)
@@ -74,7 +145,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
             tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
+            tc::mbar_init(&empty[s], 2);  // one MMA commit from each CTA of the pair
         }
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&accf[b], 1);
@@ -85,7 +156,8 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     }
     if (warp == 1) tc::tmem_alloc(tslot, 512);
     tc::tc_fence_before();
-    __syncthreads();
+    // the peer may multicast into this CTA only after its barriers exist
+    tc::cluster_sync();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
     volatile int *ab = &abort_flag;
@@ -95,17 +167,32 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             tc::tma_prefetch_desc(&tmA);
             tc::tma_prefetch_desc(&tmZ);
             int g = 0;
-            for (int cp = 0; cp < npass && !*ab; cp++) {
+            bool ok = true;
+            for (int cp = 0; cp < npass && ok; cp++) {
                 const int c = cp / P, p = cp % P;
+                const int nsl = p < P2 ? 2 : 1;
                 const int kc0 = k_lo + c * KC, kc1 = min(kc0 + KC, k_end);
                 for (int kk = kc0; kk < kc1; kk += BK, g++) {
                     const int s = g % STAGES;
                     const uint32_t ph = (g / STAGES) & 1;
-                    if (!tc::mbar_wait(&empty[s], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) break;
-                    tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                    tc::tma_load_3d(&tmA, &full[s], sA + s * A_BYTES, kk, i0, p);
-                    tc::tma_load_3d(&tmZ, &full[s], sB + s * B_BYTES, kk, j0, 0);
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) {
+                        ok = false;
+                        break;
+                    }
+                    const bool own = kk < k_own;
+                    tc::mbar_arrive_expect_tx(&full[s], (own ? A_BYTES : 0u) + uint32_t(nsl) * ZS_BYTES);
+                    if (own) tc::tma_load_3d(&tmA, &full[s], sA + s * A_BYTES, kk, i0, p);
+                    for (int q = 0; q < nsl; q++)
+                        tc::tma_load_3d_mc(&tmZ, &full[s], sB + s * B_BYTES + q * ZS_BYTES + rank * (ZS_BYTES / 2),
+                                           kk, j0 + rank * (BNO / 2), q, kPair);
                 }
+            }
+            // tail: wait until both CTAs released every stage, so that no
+            // commit of the peer is still on its way to this CTA's barriers
+            for (int t = 0; t < STAGES && ok; t++, g++) {
+                const int s = g % STAGES;
+                const uint32_t ph = (g / STAGES) & 1;
+                if (!tc::mbar_wait(&empty[s], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) break;
             }
         }
     } else if (warp == 1) {
@@ -113,7 +200,8 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             int g = 0;
             for (int cp = 0; cp < npass; cp++) {
                 const int c = cp / P, p = cp % P;
-                const int nk = (min(k_lo + (c + 1) * KC, k_end) - (k_lo + c * KC)) / BK;
+                const int kc0 = k_lo + c * KC;
+                const int nk = (min(kc0 + KC, k_end) - kc0) / BK;
                 const int buf = cp & 1;
                 const uint32_t use = cp >> 1;
                 if (!tc::mbar_wait(&acce[buf], (use & 1) ^ 1, ab, status, tc::TC_TIMEOUT_MMA)) break;
@@ -130,13 +218,15 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
-                    const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
+                    if (kc0 + kt * BK < k_own) {  // this tile's K steps are a prefix of the chunk
+                        const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
+                        const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; kk++)
-                        tc::mma_f16(d, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
-                                    idesc, (kt | kk) != 0);
-                    tc::mma_commit(&empty[s]);
+                        for (int kk = 0; kk < BK / 16; kk++)
+                            tc::mma_f16(d, tc::desc_kmajor_sw128(a0 + kk * 32),
+                                        tc::desc_kmajor_sw128(b0 + kk * 32), idesc, (kt | kk) != 0);
+                    }
+                    tc::mma_commit_mc(&empty[s], kPair);
                 }
                 tc::mma_commit(&accf[buf]);
                 if (!ok) break;
@@ -151,7 +241,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         for (int c = 0; c < 64; c++) T[c] = 0;
         bool ok = true;
         for (int cp = 0; cp < npass; cp++) {
-            const int p = cp % P;
+            const int c = cp / P, p = cp % P;
             const int buf = cp & 1;
             const uint32_t use = cp >> 1;
             if (!tc::mbar_wait(&accf[buf], use & 1, ab, status, tc::TC_TIMEOUT_EPILOGUE)) {
@@ -159,71 +249,70 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 break;
             }
             tc::tc_fence_after();
-            const bool two = p < P2;
-            const int s1 = W - (6 * (p + 1) + 8);
-            const int s2 = W - (6 * (p + 1) + 16);
-            const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 256 + half * 64);
+            // a chunk that starts at or above this tile's diagonal received no MMA
+            if (k_lo + c * KC < k_own) {
+                const bool two = p < P2;
+                const int s1 = W - (6 * (p + 1) + 8);
+                const int s2 = W - (6 * (p + 1) + 16);
+                const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 256 + half * 64);
 #pragma unroll
-            for (int c0 = 0; c0 < 64; c0 += 16) {
-                uint32_t r1[16];
-                tc::tmem_ld16(tbase + c0, r1);
-                tc::tmem_ld_wait();
-#pragma unroll
-                for (int j = 0; j < 16; j++)
-                    T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r1[j]))) << s1;
-                if (two) {
-                    uint32_t r2[16];
-                    tc::tmem_ld16(tbase + 128 + c0, r2);
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    uint32_t r1[16];
+                    tc::tmem_ld16(tbase + c0, r1);
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 16; j++)
-                        T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r2[j]))) << s2;
+                        T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r1[j]))) << s1;
+                    if (two) {
+                        uint32_t r2[16];
+                        tc::tmem_ld16(tbase + 128 + c0, r2);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; j++)
+                            T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r2[j]))) << s2;
+                    }
                 }
             }
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acce[buf]);
         }
-        if (ok) {
-            const int gi = i0 + row;
-            const int ei = e_row[gi] - W;
-            // the diagonal term Mv(i,i) Z(i,j), exactly in FP64, once: in
-            // the launch whose K range holds column i
-            const bool has_diag = gi >= k_lo && gi < k_hi;
-            const double di = has_diag ? dg[gi] : 0.0;
-            // 2 columns at a time: every load is issued before the stores
+        if (!ghost) {
+            // Final update of the 128 x 128 FP64 tile of R.  All MMAs of this
+            // CTA are complete and every stage's data has arrived, so the
+            // stage ring is free: the R tile (128 KB) and f are staged there
+            // with asynchronous copies that are all in flight at once.
+            double *Rs = reinterpret_cast<double *>(base);  // Rs[c*128 + r]
+            const int et = threadIdx.x - 64;  // 0 .. 255 over the epilogue warps
+            for (int idx = et; idx < BNO * (BM / 2); idx += 256) {
+                const int c = idx / (BM / 2), r2 = (idx % (BM / 2)) * 2;
+                cp_async16(Rs + c * BM + r2, R + i0 + r2 + int64_t(j0 + c) * ldr);
+            }
+            if (et < BNO / 4) cp_async16(fs + 4 * et, f_col + j0 + 4 * et);
+            cp_async_wait_all();
+            asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
+            if (ok) {
+                const int gi = i0 + row;
+                const int ei = e_row[gi] - W;
+                // the launch whose K range holds row i is the last to touch
+                // the row: it also writes the FP32 copy for the next solve
+                const bool last = gi >= k_lo && gi < k_hi && Yout;
 #pragma unroll
-            for (int c0 = 0; c0 < 64; c0 += 2) {
-                double rv[2];
-                int fj[2];
-                float zv[2];
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    const int gj = j0 + half * 64 + c0 + c;
-                    rv[c] = R[gi + int64_t(gj) * ldr];
-                    fj[c] = f_col[gj];
-                    zv[c] = 0.f;
-                    if (has_diag) {
-                        const int64_t zo = int64_t(gj) * ldr + gi;
-                        zv[c] = __bfloat162float(Zg[zo]) * 256.0f + __bfloat162float(Zg[zslice + zo]);
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    const int gj = j0 + half * 64 + c0 + c;
-                    double sub = ldexp(static_cast<double>(T[c0 + c]), ei + fj[c]);
-                    if (has_diag) sub += di * ldexp(double(zv[c]), fj[c] - 16);
-                    const double rn = rv[c] - sub;
-                    R[gi + int64_t(gj) * ldr] = rn;
-                    // the launch holding row i's diagonal is the last to touch
-                    // it: it also writes the FP32 copy for the next solve
-                    if (has_diag && Yout) Yout[gi + int64_t(gj) * ldr] = float(rn);
+                for (int c = 0; c < 64; c++) {
+                    const int lc = half * 64 + c;
+                    const int64_t o = gi + int64_t(j0 + lc) * ldr;
+                    // T 2^(e_i + f_j - W), rounded once
+                    const double rn = Rs[lc * BM + row] - scaled_i64_to_f64(T[c], ei + fs[lc]);
+                    R[o] = rn;
+                    if (last) Yout[o] = f64_to_f32_rn(rn);
                 }
             }
         }
     }
     tc::tc_fence_before();
     __syncthreads();
+    // neither CTA leaves while the other may still write into its shared memory
+    tc::cluster_sync();
     if (warp == 1) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, 512);
@@ -232,13 +321,13 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
 }  // namespace
 
-// R (kp x np, FP64 column-major, ldr) -= Mv * Z over k in [k_lo, k_hi),
+// R (kp x np, FP64 column-major, ldr) -= (strictly lower Mv) * Z over k in [k_lo, k_hi),
 // with A slices (7 x kp x kp BF16 row-major, contiguous) and Z slices
 // (2 x np x kp BF16: slice q holds column j of z_q at Zs + q*np*kp + j*kp).
 // kp, np multiples of 128; k_lo, k_hi multiples of 64; k_hi - k_lo <= 16384;
 // P A slices with z_1, the first P2 of them also with z_2.
 int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
-                       const double *dg, float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int P,
+                       float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int P,
                        int P2, cudaStream_t s, int *status)
 {
     if (kp <= 0 || np <= 0 || k_hi <= k_lo) return 0;
@@ -257,7 +346,7 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
     {
         uint64_t dims[3] = {uint64_t(kp), uint64_t(np), 2};
         uint64_t strides[2] = {uint64_t(kp) * 2, uint64_t(np) * uint64_t(kp) * 2};
-        uint32_t box[3] = {BK, BNO, 2};
+        uint32_t box[3] = {BK, BNO / 2, 1};  // one column half of one slice
         GB_TRY(encode_tmap(&tz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Zs, dims, strides, box));
     }
     static bool attr = false;
@@ -268,10 +357,10 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
     }
     int *st = status ? status : device_status_word();
     if (!st) return GB_STATUS_CUDA_ERROR;
-    // 1-D grid of nM*nN CTAs (grouped rasterisation)
-    const int64_t nM = kp / BM, nN = np / BNO;
-    if (nM > 65535 || nN > 65535 || nM * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
-    dim3 grid((unsigned)(nM * nN));
+    // 1-D grid of clusters of 2 over (row-tile pairs) x (column tiles)
+    const int64_t nM = kp / BM, nN = np / BNO, nMp = (nM + 1) / 2;
+    if (nM > 65535 || nN > 65535 || 2 * nMp * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
+    dim3 grid((unsigned)(2 * nMp * nN));
     // algorithmic work: P passes (P2 of them two slices wide) over the lower
     // triangle of the K range
     double tri = 0;
@@ -283,8 +372,8 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
     for (int p = 0; p < P; p++) flops += 2.0 * BM * tri * np * (p < P2 ? 2 : 1);
     LaunchScope ls(KK_RESIDUAL, s, flops, 16.0 * kp * np);
     tc_residual_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(
-        ta, tz, R, ldr, e_row, f_col, dg, static_cast<const __nv_bfloat16 *>(Zs), np * kp, Yout, (int)k_lo,
-        (int)k_hi, P, P2, W, (int)nM, (int)nN, st);
+        ta, tz, R, ldr, e_row, f_col, Yout, (int)k_lo,
+        (int)k_hi, P, P2, W, (int)nM, (int)nMp, (int)nN, st);
     return check(cudaGetLastError());
 }
 
