@@ -33,9 +33,9 @@ namespace gb {
 
 int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
                         int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s, int *status);
-int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
-                       float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int P,
-                       int P2, cudaStream_t s, int *status);
+int launch_tc_residual(long long *Tg, int64_t ldr, const void *As, const void *Zs, int64_t kp, int64_t np,
+                       int64_t k_lo, int64_t k_hi, int P, int P2, cudaStream_t s, int *status);
+int residual_weight(int P, int P2);
 int tc_gemm_prepare();
 int tc_gemm_fp8_prepare();
 int launch_tc_gemm_fp8(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
@@ -292,7 +292,7 @@ writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t
 // largest column ratio max|D~| / max|X| goes to norms[2] (as bits).
 __global__ void __launch_bounds__(256)
 slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bfloat16 *Zs, int *f_col,
-                  double *X, float *xmax, double *norms, int first, double *R, const double *dg)
+                  double *X, float *xmax, double *norms, int first)
 {
     const int64_t j = blockIdx.x;
     const float *y = Y + j * kp;
@@ -312,7 +312,6 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
     __nv_bfloat16 *z1 = Zs + j * kp;
     __nv_bfloat16 *z2 = Zs + np * kp + j * kp;
     double *x = X + j * kp;
-    double *r = R + j * kp;
     float sd = 0.f, sx = 0.f;
     for (int64_t i = threadIdx.x; i < kp; i += 256) {
         const int N = (be > 0) ? __float2int_rn(y[i] * up) : 0;
@@ -321,12 +320,8 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
         z1[i] = __int2bfloat16_rn(q1);
         z2[i] = __int2bfloat16_rn(q2);
         const float d = float(N) * down;  // exact
-        const double dd = double(d);
-        if (first) x[i] = dd;
-        else x[i] += dd;
-        // the diagonal part of the residual update, R -= Mv(i,i) D(i,j), in
-        // FP64 (the strictly lower part follows on the tensor cores)
-        r[i] = fma(-dg[i], dd, r[i]);
+        if (first) x[i] = double(d);
+        else x[i] += double(d);
         sd = fmaf(d, d, sd);
     }
     if (first) sx = sd;
@@ -355,6 +350,75 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
         atomicMax(reinterpret_cast<unsigned long long *>(&norms[2]),
                   static_cast<unsigned long long>(__double_as_longlong(ratio)));
     }
+}
+
+// ---- residual: FP64 application of the exact sums ------------------------------
+// T * 2^e rounded to the nearest double (ties to even), i.e. the value of
+// ldexp((double)T, e), for |T| < 2^63, built with integer operations (the
+// FP64 pipe retires two operations per clock and SM); results outside the
+// normal exponent range take the library path.
+__device__ __forceinline__ double scaled_i64_to_f64(long long T, int e)
+{
+    if (T == 0) return 0.0;
+    const unsigned long long sign = T < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long u = T < 0 ? 0ull - static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T);
+    const int lz = __clzll(static_cast<long long>(u));
+    int msb = 63 - lz;
+    const unsigned long long m = u << lz;  // leading one at bit 63
+    unsigned long long keep = m >> 11;     // 53 significant bits
+    const unsigned long long rem = m & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (keep & 1ull))) keep++;
+    if (keep >> 53) {  // rounded up to the next power of two
+        keep >>= 1;
+        msb++;
+    }
+    const int ex = msb + e;
+    if (ex < -1022 || ex > 1023) return ldexp(static_cast<double>(T), e);
+    return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(ex + 1023) << 52) |
+                                                       (keep & ((1ull << 52) - 1))));
+}
+// x rounded to the nearest float (ties to even), as __double2float_rn(x),
+// with integer operations; zero, subnormal, overflowing and non-finite
+// inputs take the library path.
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int ex = int((b >> 52) & 0x7FF) - 1023;
+    if (ex < -126 || ex > 127) return __double2float_rn(x);
+    const unsigned long long mant = b & ((1ull << 52) - 1);
+    unsigned int keep = static_cast<unsigned int>(mant >> 29);
+    const unsigned long long rem = mant & ((1ull << 29) - 1);
+    if (rem > (1ull << 28) || (rem == (1ull << 28) && (keep & 1u))) keep++;
+    // a carry out of the mantissa moves into the exponent field, as it must
+    const unsigned int fb = static_cast<unsigned int>((b >> 32) & 0x80000000ull) |
+                            (static_cast<unsigned int>(ex + 127) << 23);
+    return __uint_as_float(fb + keep);
+}
+
+// R(i,j) -= T(i,j) 2^(e_i + f_j - W) for the rows i >= row_lo the tensor-core
+// launch over K range [k_lo, k_hi) reached; for the rows of that range it
+// also subtracts the diagonal part Mv(i,i) D(i,j), D(i,j) = z(i,j) 2^(f_j-16)
+// with z = 256 z_1 + z_2 the correction digits (exact), in one FMA, and
+// writes Y = float(R) for the next low-precision solve (the launch holding
+// row i is the last to touch it).  One thread per element, 256 rows x 1
+// column per CTA (grid: columns x row chunks).
+__global__ void __launch_bounds__(256)
+residual_apply_kernel(double *R, const long long *Tg, const int *e_row, const int *f_col, int W, const double *dg,
+                      const __nv_bfloat16 *Zs, float *Y, int64_t kp, int64_t np, int64_t row_lo, int64_t k_lo,
+                      int64_t k_hi)
+{
+    const int64_t i = row_lo + int64_t(blockIdx.y) * 256 + threadIdx.x;
+    const int64_t j = blockIdx.x;
+    if (i >= kp) return;
+    const int64_t o = i + j * kp;
+    const int fj = f_col[j];
+    double v = R[o] - scaled_i64_to_f64(Tg[o], e_row[i] - W + fj);
+    if (i >= k_lo && i < k_hi) {
+        const int z = __bfloat162int_rn(Zs[o]) * 256 + __bfloat162int_rn(Zs[np * kp + o]);
+        v = fma(-dg[i], scaled_i64_to_f64(z, fj - 16), v);
+        Y[o] = f64_to_f32_rn(v);
+    }
+    R[o] = v;
 }
 
 // ---- workspace --------------------------------------------------------------
@@ -454,16 +518,22 @@ void pairs_for(double rho, double tol, int *P, int *P2)
     *P2 = p2;
 }
 
-// One launch per K range of at most 16384 (the int64 sums stay below 2^63);
-// inside, chunks of 4096 keep every tensor-core sum exact (|a| <= 32,
-// |z| <= 128: 4096 * 32 * 128 = 2^24).
-int residual_update(double *R, const __nv_bfloat16 *As, const __nv_bfloat16 *Zs, const int *e_row, const int *f_col,
-                    float *Y, int64_t kp, int64_t np, int P, int P2, cudaStream_t s,
-                    int *status_word)
+// One tensor-core launch per K range of at most 16384 (the int64 sums stay
+// below 2^63; inside, chunks of 4096 keep every tensor-core sum exact:
+// |a| <= 32, |z| <= 128: 4096 * 32 * 128 = 2^24), each followed by the FP64
+// application of its sums.
+int residual_update(double *R, long long *Tg, const __nv_bfloat16 *As, const __nv_bfloat16 *Zs, const int *e_row,
+                    const int *f_col, const double *dg, float *Y, int64_t kp, int64_t np, int P, int P2,
+                    cudaStream_t s, int *status_word)
 {
+    const int W = residual_weight(P, P2);
     for (int64_t lo = 0; lo < kp; lo += 16384) {
         int64_t hi = lo + 16384 < kp ? lo + 16384 : kp;
-        GB_TRY(launch_tc_residual(R, kp, As, Zs, e_row, f_col, Y, kp, np, lo, hi, P, P2, s, status_word));
+        GB_TRY(launch_tc_residual(Tg, kp, As, Zs, kp, np, lo, hi, P, P2, s, status_word));
+        LaunchScope ls(KK_CONVERT, s, 0, 30.0 * double(kp - lo) * double(np));
+        const dim3 grid((unsigned)np, (unsigned)((kp - lo + 255) / 256));
+        residual_apply_kernel<<<grid, 256, 0, s>>>(R, Tg, e_row, f_col, W, dg, Zs, Y, kp, np, lo, lo, hi);
+        GB_TRY(check(cudaGetLastError()));
     }
     return 0;
 }
@@ -554,6 +624,7 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec)
     L.o_band = take(size_t(L.kp) * kBand * 4);
     L.o_binv = take(size_t(L.kp) * kBand * 4);
     L.o_r = take(kn * 8);
+    L.o_t = take(kn * 8);
     L.o_x = take(kn * 8);
     L.o_y = take(kn * 4);
     L.o_ybf = take(kn * 2);
@@ -605,6 +676,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
     auto *band = reinterpret_cast<float *>(ws + o_band);
     auto *binv = reinterpret_cast<float *>(ws + o_binv);
     auto *R = reinterpret_cast<double *>(ws + o_r);
+    auto *Tg = reinterpret_cast<long long *>(ws + L.o_t);
     auto *X = reinterpret_cast<double *>(ws + o_x);
     auto *Y = reinterpret_cast<float *>(ws + o_y);
     auto *Ybf = reinterpret_cast<__nv_bfloat16 *>(ws + o_ybf);
@@ -670,7 +742,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
             {
                 LaunchScope ls(KK_CONVERT, s, 0, 20.0 * double(nel));
                 slice_cols_kernel<<<(unsigned)np, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms,
-                                                                t == 0, R, dg);
+                                                                t == 0);
                 if ((st = check(cudaGetLastError()))) break;
             }
             if ((st = check(cudaMemcpyAsync(h_norm, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)))) break;
@@ -702,7 +774,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
             int P = 7, P2 = 6;
             pairs_for(t == 0 ? 1.0 : h_norm[2], tol, &P, &P2);
             Lmax = P * 10 + P2;  // recorded in the history as 10*P + P2
-            if ((st = residual_update(R, As, Zs, e_row, f_col, Y, kp, np, P, P2, s, status_word))) break;
+            if ((st = residual_update(R, Tg, As, Zs, e_row, f_col, dg, Y, kp, np, P, P2, s, status_word))) break;
         }
         if (st) break;
         {

@@ -14,9 +14,11 @@
 // sum S_pq = sum_k a_p z_q of a chunk is an exact integer of at most 2^24 in
 // the FP32 accumulator.  The epilogue converts S_pq to integers and adds
 // S_pq 2^(W - 6p - 8q) into int64 sums T (W = the largest weight exponent
-// formed; with K <= 16384 per launch, |T| < 4 * 2^60.1 < 2^63), then
-// applies R -= 2^(e_i + f_j - W) T in FP64: the one rounding of the whole
-// product is that of T to FP64.
+// formed; with K <= 16384 per launch, |T| < 4 * 2^60.1 < 2^63) and stores
+// T; a separate elementwise pass applies R -= 2^(e_i + f_j - W) T in FP64
+// (the one rounding of the whole product is that of T to FP64).  The FP64
+// pipe of an SM retires two operations per clock: done here, that work
+// would idle the tensor cores of the SM for tens of microseconds per tile.
 //
 // One CTA per 128 x 128 tile of R; the CTAs run in clusters of two that
 // hold vertically adjacent row tiles of the same columns, so both need the
@@ -50,64 +52,10 @@ constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr size_t SMEM_BYTES = 1024 + STAGES * size_t(STAGE_BYTES) + 256;
 constexpr int NTHREADS = 320;
 constexpr uint16_t kPair = 0x3;
-static_assert(BM * BNO * 8 <= STAGES * STAGE_BYTES, "final staging fits the ring");
-
-// The FP64 pipe of an sm_103 SM retires two operations per clock, so the
-// final update builds its doubles with integer operations instead of
-// conversions and ldexp:
-// T * 2^e rounded to the nearest double (ties to even), i.e. the value of
-// ldexp((double)T, e), for |T| < 2^63.  Results outside the normal exponent
-// range take the library path.
-__device__ __forceinline__ double scaled_i64_to_f64(long long T, int e)
-{
-    if (T == 0) return 0.0;
-    const unsigned long long sign = T < 0 ? (1ull << 63) : 0ull;
-    const unsigned long long u = T < 0 ? 0ull - static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T);
-    const int lz = __clzll(static_cast<long long>(u));
-    int msb = 63 - lz;
-    const unsigned long long m = u << lz;  // leading one at bit 63
-    unsigned long long keep = m >> 11;     // 53 significant bits
-    const unsigned long long rem = m & 0x7FFull;
-    if (rem > 0x400ull || (rem == 0x400ull && (keep & 1ull))) keep++;
-    if (keep >> 53) {  // rounded up to the next power of two
-        keep >>= 1;
-        msb++;
-    }
-    const int ex = msb + e;
-    if (ex < -1022 || ex > 1023) return ldexp(static_cast<double>(T), e);
-    return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(ex + 1023) << 52) |
-                                                       (keep & ((1ull << 52) - 1))));
-}
-// x rounded to the nearest float (ties to even), as __double2float_rn(x);
-// zero, subnormal, overflowing and non-finite inputs take the library path.
-__device__ __forceinline__ float f64_to_f32_rn(double x)
-{
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const int ex = int((b >> 52) & 0x7FF) - 1023;
-    if (ex < -126 || ex > 127) return __double2float_rn(x);
-    const unsigned long long mant = b & ((1ull << 52) - 1);
-    unsigned int keep = static_cast<unsigned int>(mant >> 29);
-    const unsigned long long rem = mant & ((1ull << 29) - 1);
-    if (rem > (1ull << 28) || (rem == (1ull << 28) && (keep & 1u))) keep++;
-    // a carry out of the mantissa moves into the exponent field, as it must
-    const unsigned int fb = static_cast<unsigned int>((b >> 32) & 0x80000000ull) |
-                            (static_cast<unsigned int>(ex + 127) << 23);
-    return __uint_as_float(fb + keep);
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ,
-                   double *__restrict__ R, int64_t ldr, const int *__restrict__ e_row,
-                   const int *__restrict__ f_col, float *__restrict__ Yout, int k_lo,
+                   long long *__restrict__ Tg, int64_t ldr, int k_lo,
                    int k_hi, int P, int P2, int W, int nMt, int nMp, int nNt, int *status)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -120,7 +68,6 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint64_t *acce = accf + 2;        // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + 2);
     __shared__ int abort_flag;
-    __shared__ __align__(16) int fs[BNO];  // f_col of the tile's columns (final update)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rank = int(tc::cluster_ctarank());
@@ -277,36 +224,12 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acce[buf]);
         }
-        if (!ghost) {
-            // Final update of the 128 x 128 FP64 tile of R.  All MMAs of this
-            // CTA are complete and every stage's data has arrived, so the
-            // stage ring is free: the R tile (128 KB) and f are staged there
-            // with asynchronous copies that are all in flight at once.
-            double *Rs = reinterpret_cast<double *>(base);  // Rs[c*128 + r]
-            const int et = threadIdx.x - 64;  // 0 .. 255 over the epilogue warps
-            for (int idx = et; idx < BNO * (BM / 2); idx += 256) {
-                const int c = idx / (BM / 2), r2 = (idx % (BM / 2)) * 2;
-                cp_async16(Rs + c * BM + r2, R + i0 + r2 + int64_t(j0 + c) * ldr);
-            }
-            if (et < BNO / 4) cp_async16(fs + 4 * et, f_col + j0 + 4 * et);
-            cp_async_wait_all();
-            asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
-            if (ok) {
-                const int gi = i0 + row;
-                const int ei = e_row[gi] - W;
-                // the launch whose K range holds row i is the last to touch
-                // the row: it also writes the FP32 copy for the next solve
-                const bool last = gi >= k_lo && gi < k_hi && Yout;
+        if (ok && !ghost) {
+            // the exact sums of this tile: lanes hold consecutive rows, so
+            // each store instruction writes 256 contiguous bytes
+            const int64_t o = i0 + row + int64_t(j0 + half * 64) * ldr;
 #pragma unroll
-                for (int c = 0; c < 64; c++) {
-                    const int lc = half * 64 + c;
-                    const int64_t o = gi + int64_t(j0 + lc) * ldr;
-                    // T 2^(e_i + f_j - W), rounded once
-                    const double rn = Rs[lc * BM + row] - scaled_i64_to_f64(T[c], ei + fs[lc]);
-                    R[o] = rn;
-                    if (last) Yout[o] = f64_to_f32_rn(rn);
-                }
-            }
+            for (int c = 0; c < 64; c++) Tg[o + int64_t(c) * ldr] = T[c];
         }
     }
     tc::tc_fence_before();
@@ -321,20 +244,25 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
 }  // namespace
 
-// R (kp x np, FP64 column-major, ldr) -= (strictly lower Mv) * Z over k in [k_lo, k_hi),
-// with A slices (7 x kp x kp BF16 row-major, contiguous) and Z slices
+// Exponent of the largest pair weight formed (pair (p, q) has weight
+// 2^-(6p + 8q)): the int64 sums T carry it as 2^W.
+int residual_weight(int P, int P2) { return (P2 > 0 && 6 * P2 + 16 > 6 * P + 8) ? 6 * P2 + 16 : 6 * P + 8; }
+
+// T (kp x np, int64 column-major, ldr) = the exact digit sums of
+// (strictly lower Mv) * Z over k in [k_lo, k_hi) for the row tiles the range
+// reaches (rows >= k_lo), scaled by 2^(W - e_i - f_j) with W from
+// residual_weight(P, P2); A slices (7 x kp x kp BF16 row-major, contiguous) and Z slices
 // (2 x np x kp BF16: slice q holds column j of z_q at Zs + q*np*kp + j*kp).
 // kp, np multiples of 128; k_lo, k_hi multiples of 64; k_hi - k_lo <= 16384;
 // P A slices with z_1, the first P2 of them also with z_2.
-int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, const int *e_row, const int *f_col,
-                       float *Yout, int64_t kp, int64_t np, int64_t k_lo, int64_t k_hi, int P,
-                       int P2, cudaStream_t s, int *status)
+int launch_tc_residual(long long *Tg, int64_t ldr, const void *As, const void *Zs, int64_t kp, int64_t np,
+                       int64_t k_lo, int64_t k_hi, int P, int P2, cudaStream_t s, int *status)
 {
     if (kp <= 0 || np <= 0 || k_hi <= k_lo) return 0;
     if (kp % 128 || np % 128 || k_lo % 64 || k_hi % 64 || k_hi - k_lo > 16384 || P < 1 || P > 7 || P2 < 0 ||
         P2 > P)
         return GB_STATUS_CUDA_ERROR;
-    const int W = (P2 > 0 && 6 * P2 + 16 > 6 * P + 8) ? 6 * P2 + 16 : 6 * P + 8;
+    const int W = residual_weight(P, P2);
     if (kp > 0x7fffffffLL || np > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     CUtensorMap ta, tz;
     {
@@ -370,9 +298,9 @@ int launch_tc_residual(double *R, int64_t ldr, const void *As, const void *Zs, c
     }
     double flops = 0;
     for (int p = 0; p < P; p++) flops += 2.0 * BM * tri * np * (p < P2 ? 2 : 1);
-    LaunchScope ls(KK_RESIDUAL, s, flops, 16.0 * kp * np);
+    LaunchScope ls(KK_RESIDUAL, s, flops, 8.0 * kp * np);
     tc_residual_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(
-        ta, tz, R, ldr, e_row, f_col, Yout, (int)k_lo,
+        ta, tz, Tg, ldr, (int)k_lo,
         (int)k_hi, P, P2, W, (int)nM, (int)nMp, (int)nN, st);
     return check(cudaGetLastError());
 }
