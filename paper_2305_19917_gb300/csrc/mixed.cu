@@ -11,8 +11,8 @@
 // The residual is carried incrementally: after X += D~ (D~ = D rounded to
 // the two 8-bit digits per column that the residual kernel consumes),
 // R -= Mv D~, so R stays the residual of the X actually held.  Mv is cut
-// without its diagonal into seven 6-bit digit slices with a power-of-two
-// scale per row (42 bits of the largest off-diagonal entry); the diagonal
+// without its diagonal into six 8-bit digit slices with a power-of-two
+// scale per row (48 bits of the largest off-diagonal entry); the diagonal
 // term is applied exactly in FP64;
 // the number of slice pairs formed shrinks as the corrections shrink.
 //
@@ -50,7 +50,7 @@ int launch_apply_inverse(const float *Linv_b, float *Yb, int64_t ldy, __nv_bfloa
 
 namespace {
 
-constexpr int kSlices = 7;     // digit slices of Mv (6 bits each)
+constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
 constexpr int kBand = 128;     // FP32 band of diagonal 128-blocks (column-major per block)
 
 // Canonical forward view of the user problem (device-side description).
@@ -175,16 +175,16 @@ __device__ __forceinline__ __nv_bfloat16 d2bf16(double a)
     return __ushort_as_bfloat16(out);
 }
 
-// The 42-bit fixed-point value N = round(a 2^(42-e)) of |a| < 2^(e-1)
-// (|N| <= 2^41), computed from the bit pattern with integer operations.
-__device__ __forceinline__ long long fixed42(double a, int e)
+// The 48-bit fixed-point value N = round(a 2^(48-e)) of |a| < 2^(e-1)
+// (|N| <= 2^47), computed from the bit pattern with integer operations.
+__device__ __forceinline__ long long fixed48(double a, int e)
 {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a));
     const int E = int((b >> 52) & 0x7FF);
-    if (E == 0) return 0;  // zero (subnormals are far below 2^-42 of any row scale)
+    if (E == 0) return 0;  // zero (subnormals are far below 2^-48 of any row scale)
     const unsigned long long mant = (b & ((1ull << 52) - 1)) | (1ull << 52);  // a = mant 2^(E-1075)
-    // a 2^(42-e) = mant 2^(E - 1075 + 42 - e): right shift by r = 1033 + e - E
-    const int r = 1033 + e - E;
+    // a 2^(48-e) = mant 2^(E - 1075 + 48 - e): right shift by r = 1027 + e - E
+    const int r = 1027 + e - E;
     long long n;
     if (r >= 63) n = 0;
     else if (r <= 0) n = (long long)(mant << (-r));  // cannot happen for |a| < 2^(e-1)
@@ -192,7 +192,7 @@ __device__ __forceinline__ long long fixed42(double a, int e)
     return (b >> 63) ? -n : n;
 }
 
-// Pass 2: BF16 copy (round to nearest), the 7 digit slices of the strictly
+// Pass 2: BF16 copy (round to nearest), the 6 digit slices of the strictly
 // lower part, the FP64 diagonal and the FP32 band of diagonal 64-blocks.
 __global__ void __launch_bounds__(256)
 prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bfloat16 *As, float *band,
@@ -214,17 +214,17 @@ prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bflo
         if (A8 && (c >> 7) < (i >> 7))
             A8[off] = __nv_cvt_float_to_fp8(float(a) / bscale[(i >> 7) * (kp >> 7) + (c >> 7)], __NV_SATFINITE,
                                             __NV_E4M3);
-        // balanced base-64 digits of N = round(a 2^(42-e)): N = sum_p q_p 64^(7-p),
-        // q_p in [-32, 32]; least significant first
-        long long N = (c == i) ? 0 : fixed42(a, e_row[i]);
+        // balanced base-256 digits of N = round(a 2^(48-e)): N = sum_p q_p 256^(6-p),
+        // q_p in [-128, 128]; least significant first
+        long long N = (c == i) ? 0 : fixed48(a, e_row[i]);
         if (c == i) dg[i] = a;
 #pragma unroll
         for (int p = kSlices - 1; p >= 1; p--) {
-            const long long d = ((N + 32) & 63) - 32;
-            As[p * slice + off] = __int2bfloat16_rn(int(d));  // exact: |d| <= 32
-            N = (N - d) >> 6;
+            const long long d = ((N + 128) & 255) - 128;
+            As[p * slice + off] = __int2bfloat16_rn(int(d));  // exact: |d| <= 128 has <= 8 significant bits
+            N = (N - d) >> 8;
         }
-        As[off] = __int2bfloat16_rn(int(N));  // top digit, |N| <= 32
+        As[off] = __int2bfloat16_rn(int(N));  // top digit, |N| <= 128
         if (c / kBand == i / kBand) band[size_t(c) * kBand + (i % kBand)] = float(a);
     }
 }
@@ -498,8 +498,8 @@ int low_solve(LowExec &e, int64_t kp)
 }
 
 // Which digit pairs the residual must form for a correction Z whose size
-// relative to X is rho.  Pair (p, q) has weight 2^-(6p + 8q), i.e. it sits
-// 2^-(6p + 8q - 14) below the leading pair (1, 1), and the leading pair is
+// relative to X is rho.  Pair (p, q) has weight 2^-(8p + 8q), i.e. it sits
+// 2^-(8p + 8q - 16) below the leading pair (1, 1), and the leading pair is
 // about rho |Mv||X|; every pair above 2^-target |Mv||X| is formed, with
 // target = log2(1/tol) + 2 (a factor 4 under the requested tolerance).
 // Returns P (slices paired with z_1) and P2 (slices also paired with z_2).
@@ -507,10 +507,10 @@ void pairs_for(double rho, double tol, int *P, int *P2)
 {
     const double target = -std::log2(tol > 0 ? tol : 1e-16) + 2.0;
     const double b = rho > 0 ? -std::log2(rho) : 1e9;
-    const double budget = target - b + 14.0;
-    int p1 = int(std::floor((budget - 8.0) / 6.0));
-    int p2 = int(std::floor((budget - 16.0) / 6.0));
-    if (p1 > 7) p1 = 7;
+    const double budget = target - b + 16.0;
+    int p1 = int(std::floor((budget - 8.0) / 8.0));
+    int p2 = int(std::floor((budget - 16.0) / 8.0));
+    if (p1 > kSlices) p1 = kSlices;
     if (p1 < 1) p1 = 1;
     if (p2 > p1) p2 = p1;
     if (p2 < 0) p2 = 0;
@@ -519,8 +519,8 @@ void pairs_for(double rho, double tol, int *P, int *P2)
 }
 
 // One tensor-core launch per K range of at most 16384 (the int64 sums stay
-// below 2^63; inside, chunks of 4096 keep every tensor-core sum exact:
-// |a| <= 32, |z| <= 128: 4096 * 32 * 128 = 2^24), each followed by the FP64
+// below 2^63; inside, chunks of 1024 keep every tensor-core sum exact:
+// |a| <= 128, |z| <= 128: 1024 * 128 * 128 = 2^24), each followed by the FP64
 // application of its sums.
 int residual_update(double *R, long long *Tg, const __nv_bfloat16 *As, const __nv_bfloat16 *Zs, const int *e_row,
                     const int *f_col, const double *dg, float *Y, int64_t kp, int64_t np, int P, int P2,
@@ -771,7 +771,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
                 if (t >= max_iter) break;
                 prev_rho = rho;
             }
-            int P = 7, P2 = 6;
+            int P = kSlices, P2 = kSlices - 1;
             pairs_for(t == 0 ? 1.0 : h_norm[2], tol, &P, &P2);
             Lmax = P * 10 + P2;  // recorded in the history as 10*P + P2
             if ((st = residual_update(R, Tg, As, Zs, e_row, f_col, dg, Y, kp, np, P, P2, s, status_word))) break;

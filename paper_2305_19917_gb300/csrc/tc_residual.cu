@@ -4,17 +4,18 @@
 //
 // where both factors are given as fixed-point digit slices (BF16 holding
 // small integers), the strictly lower part of Mv as
-//     Mv(i,k) = 2^e_i * sum_{p=1..7} a_p(i,k) 2^(-6p),   |a_p| <= 32
+//     Mv(i,k) = 2^e_i * sum_{p=1..6} a_p(i,k) 2^(-8p),   |a_p| <= 128
 // (the diagonal part R -= Mv(i,i) Z(i,j) is applied in FP64 where the
 // correction digits are formed, outside this kernel), and
 //     Z(k,j)  = 2^f_j * sum_{q=1..2} z_q(k,j) 2^(-8q),   |z_q| <= 128,
-// and only the pairs with 6p + 8q <= budget are formed: slices p = 1..P with
-// z_1, and p = 1..P2 also with z_2.  Each digit product is at most 2^12 and
-// the K range is accumulated in chunks of at most 4096, so every tensor-core
+// and only the pairs with 8p + 8q <= budget are formed: slices p = 1..P with
+// z_1, and p = 1..P2 also with z_2.  Each digit product is at most 2^14 and
+// the K range is accumulated in chunks of at most 1024, so every tensor-core
 // sum S_pq = sum_k a_p z_q of a chunk is an exact integer of at most 2^24 in
 // the FP32 accumulator.  The epilogue converts S_pq to integers and adds
-// S_pq 2^(W - 6p - 8q) into int64 sums T (W = the largest weight exponent
-// formed; with K <= 16384 per launch, |T| < 4 * 2^60.1 < 2^63) and stores
+// S_pq 2^(W - 8p - 8q) into int64 sums T (W = the largest weight exponent
+// formed, so |S_pq 2^(W-8p-8q)| <= 2^(24+W-16) <= 2^56; with K <= 16384 per
+// launch, i.e. at most 16 chunks, |T| < 16 * 1.01 * 2^56 < 2^61) and stores
 // T; a separate elementwise pass applies R -= 2^(e_i + f_j - W) T in FP64
 // (the one rounding of the whole product is that of T to FP64).  The FP64
 // pipe of an SM retires two operations per clock: done here, that work
@@ -45,6 +46,7 @@ int *device_status_word();
 namespace {
 
 constexpr int BM = 128, BNO = 128, BK = 64, STAGES = 4;
+constexpr int kASlices = 6;                        // digit slices of Mv (8 bits each)
 constexpr uint32_t A_BYTES = BM * BK * 2;          // one A slice tile
 constexpr uint32_t ZS_BYTES = BNO * BK * 2;        // one Z slice tile (128 columns)
 constexpr uint32_t B_BYTES = 2 * ZS_BYTES;         // z_1 and z_2 tiles
@@ -82,10 +84,10 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const int k_end = min(k_hi, m0 * BM + BM);                 // the pair's K range
     const int k_own = ghost ? k_lo : min(k_hi, i0 + BM);       // this tile's
     if (k_end <= k_lo) return;  // both tiles entirely above the diagonal
-    // exactness needs K <= 4096 per tensor-memory accumulation: the K range
-    // is cut into chunks of at most 4096, each pass of each chunk drained
-    // separately into the same int64 sums (|T| < 4 * 2^60.1 over 4 chunks)
-    constexpr int KC = 4096;
+    // exactness needs K <= 1024 per tensor-memory accumulation: the K range
+    // is cut into chunks of at most 1024, each pass of each chunk drained
+    // separately into the same int64 sums
+    constexpr int KC = 1024;
     const int nchunks = (k_end - k_lo + KC - 1) / KC;
     const int npass = nchunks * P;
 
@@ -199,8 +201,8 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             // a chunk that starts at or above this tile's diagonal received no MMA
             if (k_lo + c * KC < k_own) {
                 const bool two = p < P2;
-                const int s1 = W - (6 * (p + 1) + 8);
-                const int s2 = W - (6 * (p + 1) + 16);
+                const int s1 = W - (8 * (p + 1) + 8);
+                const int s2 = W - (8 * (p + 1) + 16);
                 const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 256 + half * 64);
 #pragma unroll
                 for (int c0 = 0; c0 < 64; c0 += 16) {
@@ -245,13 +247,13 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 }  // namespace
 
 // Exponent of the largest pair weight formed (pair (p, q) has weight
-// 2^-(6p + 8q)): the int64 sums T carry it as 2^W.
-int residual_weight(int P, int P2) { return (P2 > 0 && 6 * P2 + 16 > 6 * P + 8) ? 6 * P2 + 16 : 6 * P + 8; }
+// 2^-(8p + 8q)): the int64 sums T carry it as 2^W.
+int residual_weight(int P, int P2) { return (P2 > 0 && 8 * P2 + 16 > 8 * P + 8) ? 8 * P2 + 16 : 8 * P + 8; }
 
 // T (kp x np, int64 column-major, ldr) = the exact digit sums of
 // (strictly lower Mv) * Z over k in [k_lo, k_hi) for the row tiles the range
 // reaches (rows >= k_lo), scaled by 2^(W - e_i - f_j) with W from
-// residual_weight(P, P2); A slices (7 x kp x kp BF16 row-major, contiguous) and Z slices
+// residual_weight(P, P2); A slices (6 x kp x kp BF16 row-major, contiguous) and Z slices
 // (2 x np x kp BF16: slice q holds column j of z_q at Zs + q*np*kp + j*kp).
 // kp, np multiples of 128; k_lo, k_hi multiples of 64; k_hi - k_lo <= 16384;
 // P A slices with z_1, the first P2 of them also with z_2.
@@ -259,14 +261,14 @@ int launch_tc_residual(long long *Tg, int64_t ldr, const void *As, const void *Z
                        int64_t k_lo, int64_t k_hi, int P, int P2, cudaStream_t s, int *status)
 {
     if (kp <= 0 || np <= 0 || k_hi <= k_lo) return 0;
-    if (kp % 128 || np % 128 || k_lo % 64 || k_hi % 64 || k_hi - k_lo > 16384 || P < 1 || P > 7 || P2 < 0 ||
+    if (kp % 128 || np % 128 || k_lo % 64 || k_hi % 64 || k_hi - k_lo > 16384 || P < 1 || P > kASlices || P2 < 0 ||
         P2 > P)
         return GB_STATUS_CUDA_ERROR;
     const int W = residual_weight(P, P2);
     if (kp > 0x7fffffffLL || np > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     CUtensorMap ta, tz;
     {
-        uint64_t dims[3] = {uint64_t(kp), uint64_t(kp), 7};
+        uint64_t dims[3] = {uint64_t(kp), uint64_t(kp), uint64_t(kASlices)};
         uint64_t strides[2] = {uint64_t(kp) * 2, uint64_t(kp) * uint64_t(kp) * 2};
         uint32_t box[3] = {BK, BM, 1};
         GB_TRY(encode_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, As, dims, strides, box));
