@@ -356,8 +356,9 @@ def run_ours(args):
         peak, bound = FP64_PEAK_TFLOPS, "alu"
         src = ("derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json; "
                "probe measured 1.196 TF/s DFMA)")
+    traffic = RESIDUAL_DRAM_BYTES.get((m, n, args.prec)) if (mixed and dom == "residual") else None
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "frac": achieved / peak, "traffic": traffic, "peak_source": src,
                 "launches": p["launches"], "ms_total": p["ms"],
                 "share": p["ms"] / max(1e-9, sum(v["ms"] for v in prof.values()))}
 
@@ -393,6 +394,12 @@ def run_ours(args):
         dist.destroy_process_group()
     return 0
 
+
+# DRAM bytes (read + write) per launch of the residual kernel, from one ncu
+# capture of the full-size workload (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean of the two launches of one solve).  Only valid for the kernel as it was
+# when captured; drop the entry when the kernel changes.
+RESIDUAL_DRAM_BYTES = {(16384, 16384, "bf16"): 19.17e9}
 
 # FP32 ALU peak for the batched FP32 roofline: 152 SMs x 128 FFMA/clk x 2
 # flop x 2.07 GHz (an FFMA probe measured 69.8 TFLOP/s).
