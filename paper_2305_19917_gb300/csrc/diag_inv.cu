@@ -47,7 +47,8 @@ __host__ __device__ constexpr int strip_off(int g) { return 8 * g * (g + 1); }
 
 // One CTA (128 threads) per diagonal block: thread j forms column j of L^-1
 // by forward substitution on e_j (row form, FP32, two partial sums).
-__global__ void __launch_bounds__(NBI) invert_blocks_kernel(const float *__restrict__ band, float *__restrict__ inv)
+__global__ void __launch_bounds__(NBI) invert_blocks_kernel(const float *__restrict__ band, float *__restrict__ inv,
+                                                            __nv_bfloat16 *__restrict__ inv16, int64_t kp)
 {
     extern __shared__ __align__(16) float sm[];
     float *L = sm;                // L[i*NBI + k] = L(i,k)   (row-major for the dot form)
@@ -81,6 +82,18 @@ __global__ void __launch_bounds__(NBI) invert_blocks_kernel(const float *__restr
     for (int g = 0; g < NSTRIP; g++) {
         const int cnt = (4 * g + 4) * 4;
         for (int e = j; e < cnt; e += NBI) Ib[strip_off(g) + e] = X[(4 * g + (e & 3)) * (NBI + 1) + (e >> 2)];
+    }
+    // two-term BF16 split L^-1 = hi + lo, row-major (K-major for the tensor
+    // cores): hi rows at block*128 + i, lo rows at kp + block*128 + i
+    if (inv16) {
+        const int64_t r0 = int64_t(blockIdx.x) * NBI;
+        for (int idx = j; idx < NBI * NBI; idx += NBI) {
+            const int i = idx / NBI, k = idx % NBI;
+            const float x = X[i * (NBI + 1) + k];
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            inv16[(r0 + i) * NBI + k] = h;
+            inv16[(kp + r0 + i) * NBI + k] = __float2bfloat16_rn(x - __bfloat162float(h));
+        }
     }
 }
 
@@ -243,13 +256,15 @@ int diag_inv_prepare()
     return 0;
 }
 
-// Invert the nblocks diagonal blocks held in `band` into `inv` (same layout).
-int launch_invert_blocks(const float *band, float *inv, int64_t nblocks, cudaStream_t s)
+// Invert the nblocks diagonal blocks held in `band` into `inv` (strips) and,
+// when inv16 is given, into its two-term BF16 split (2 x kp x 128, kp =
+// 128 * nblocks rows of 128).
+int launch_invert_blocks(const float *band, float *inv, __nv_bfloat16 *inv16, int64_t nblocks, cudaStream_t s)
 {
     if (nblocks <= 0) return 0;
     GB_TRY(diag_inv_prepare());
     LaunchScope ls(KK_DIAG, s, double(nblocks) * NBI * NBI * NBI / 3.0, 8.0 * nblocks * NBI * NBI);
-    invert_blocks_kernel<<<(unsigned)nblocks, NBI, INV_SMEM, s>>>(band, inv);
+    invert_blocks_kernel<<<(unsigned)nblocks, NBI, INV_SMEM, s>>>(band, inv, inv16, int64_t(nblocks) * NBI);
     return check(cudaGetLastError());
 }
 

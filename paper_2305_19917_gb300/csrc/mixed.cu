@@ -44,7 +44,10 @@ int launch_tc_gemm_fp8(int64_t M, int64_t N, int64_t K, const void *A, int64_t l
 int launch_apply_inverse_fp8(const float *Linv_b, float *Yb, int64_t ldy, uint8_t *Y8_b, float *s8_b, int nr,
                              int64_t ncols, cudaStream_t s);
 int diag_inv_prepare();
-int launch_invert_blocks(const float *band, float *inv, int64_t nblocks, cudaStream_t s);
+int launch_invert_blocks(const float *band, float *inv, __nv_bfloat16 *inv16, int64_t nblocks, cudaStream_t s);
+int apply_tc_prepare();
+int launch_apply_inverse_tc(const __nv_bfloat16 *inv16, int64_t kp, int64_t b, float *Yb, int64_t ldy,
+                            __nv_bfloat16 *Ybf_b, int nr, int64_t ncols, cudaStream_t s, int *status);
 int launch_apply_inverse(const float *Linv_b, float *Yb, int64_t ldy, __nv_bfloat16 *Ybf_b, int nr, int64_t ncols,
                          cudaStream_t s);
 
@@ -461,6 +464,7 @@ struct LowExec {
     const float *sA = nullptr;   // (kp/128)^2 block scales of A8
     uint8_t *Y8 = nullptr;
     float *sY = nullptr;         // (kp/128) x (np/64) block scales of Y8
+    const __nv_bfloat16 *binv16 = nullptr;  // two-term BF16 split of the inverses (tensor-core TS task)
     int status = 0;
     bool ok() const { return status == 0; }
     void ts(int64_t b0, int64_t nr, float a)
@@ -474,6 +478,9 @@ struct LowExec {
         if (fp8)
             status = launch_apply_inverse_fp8(binv + b0 * kBand, Y + b0, kp, Y8 + b0, sY + (b0 / 128) * (np / 64),
                                               (int)nr, np, s);
+        else if (binv16)
+            status = launch_apply_inverse_tc(binv16, kp, b0 / kBand, Y + b0, kp, Ybf + b0, (int)nr, np, s,
+                                             status_word);
         else
             status = launch_apply_inverse(binv + b0 * kBand, Y + b0, kp, Ybf + b0, (int)nr, np, s);
     }
@@ -571,6 +578,7 @@ int low_graph(LowExec &le, const void *ws, LowGraph **out)
     GB_TRY(tc_gemm_prepare());
     GB_TRY(tc_gemm_fp8_prepare());
     GB_TRY(diag_inv_prepare());
+    GB_TRY(apply_tc_prepare());
     cudaStream_t user = le.s;
     le.s = cap_stream[dev];
     le.status = 0;
@@ -623,6 +631,7 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec)
     L.o_as = take(kk * 2 * kSlices);
     L.o_band = take(size_t(L.kp) * kBand * 4);
     L.o_binv = take(size_t(L.kp) * kBand * 4);
+    L.o_binv16 = take(size_t(L.kp) * kBand * 4);
     L.o_r = take(kn * 8);
     L.o_t = take(kn * 8);
     L.o_x = take(kn * 8);
@@ -717,8 +726,10 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
                 B, ldb, side == GB_LEFT, !forward, k, ncols, alpha, R, Y, kp);
             if ((st = check(cudaGetLastError()))) break;
         }
-        if ((st = launch_invert_blocks(band, binv, kp / kBand, s))) break;
+        auto *binv16 = fp8 ? nullptr : reinterpret_cast<__nv_bfloat16 *>(ws + L.o_binv16);
+        if ((st = launch_invert_blocks(band, binv, binv16, kp / kBand, s))) break;
         LowExec le{Y, Ybf, Abf, binv, kp, np, s, status_word};
+        le.binv16 = binv16;
         le.fp8 = fp8;
         le.A8 = A8;
         le.sA = bscale;
