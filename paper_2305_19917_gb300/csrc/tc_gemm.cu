@@ -223,22 +223,28 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     }
 }
 
-// Persistent form for wide updates: one CTA per SM walks the 128 x 256 tiles
-// t = blockIdx.x, blockIdx.x + gridDim.x, ... (grouped rasterisation) with
-// two TMEM accumulators (2 x 256 columns), so that the epilogue of one tile
-// runs while the MMAs of the next accumulate into the other buffer.  The TMA
-// ring runs continuously across tiles.  320 threads: warp 0 TMA, warp 1 MMA,
-// warps 2-9 epilogue (warps w and w+4 share TMEM lane quadrant w % 4 and
-// take one half of the tile's columns each).
-constexpr int PBN = 256, PSTAGES = 4;
-constexpr uint32_t P_B_BYTES = PBN * BK * 2, P_STAGE_BYTES = A_BYTES + P_B_BYTES;
-constexpr size_t P_SMEM_BYTES = 1024 + PSTAGES * size_t(P_STAGE_BYTES) + 256;
+// Persistent form: one CTA per SM walks the 128 x PBN tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (grouped rasterisation) with two TMEM
+// accumulators (2 x PBN columns), so that the epilogue of one tile runs while
+// the MMAs of the next accumulate into the other buffer.  The TMA ring (about
+// 192 KB, sized to K when K is short) runs continuously across tiles.  320
+// threads: warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (warps w and w+4 share
+// TMEM lane quadrant w % 4 and take one half of the tile's columns each).
+template <int PBN>
+struct PCfg {
+    static constexpr uint32_t B_BYTES = PBN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 8 ? 8 : (192 * 1024) / STAGE_BYTES;
+    static constexpr uint32_t TMEM_COLS = 2 * PBN < 32 ? 32 : 2 * PBN;
+    static size_t smem_for(int nst) { return 1024 + nst * size_t(STAGE_BYTES) + 256; }
+};
 
+template <int PBN>
 __global__ void __launch_bounds__(320, 1)
 tc_gemm_bf16_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                                float *__restrict__ C, int64_t ldc, int M, int N, int K, float alpha, int nMt,
-                               int nNt, int *status)
+                               int nNt, int PSTAGES, int *status)
 {
+    constexpr uint32_t P_B_BYTES = PCfg<PBN>::B_BYTES, P_STAGE_BYTES = PCfg<PBN>::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = base;
@@ -266,7 +272,7 @@ tc_gemm_bf16_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __
         abort_flag = 0;
         tc::fence_barrier_init();
     }
-    if (warp == 1) tc::tmem_alloc(tslot, 2 * PBN);
+    if (warp == 1) tc::tmem_alloc(tslot, PCfg<PBN>::TMEM_COLS);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -364,7 +370,7 @@ tc_gemm_bf16_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __
     __syncthreads();
     if (warp == 1) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, 2 * PBN);
+        tc::tmem_dealloc(tmem, PCfg<PBN>::TMEM_COLS);
     }
 }
 
@@ -384,12 +390,14 @@ static int prepare_bn()
 
 // One-time per-process set-up (kernel attributes, device status word); must
 // run before any stream capture that launches the kernel.
+template <int PBN>
 static int prepare_persistent()
 {
     static bool attr = false;
     if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(tc_gemm_bf16_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)P_SMEM_BYTES));
+        GB_CUDA(cudaFuncSetAttribute(tc_gemm_bf16_persistent_kernel<PBN>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)PCfg<PBN>::smem_for(PCfg<PBN>::STAGES)));
         attr = true;
     }
     return 0;
@@ -406,10 +414,10 @@ static int num_sms()
 
 int tc_gemm_prepare()
 {
-    GB_TRY(prepare_persistent());
+    GB_TRY(prepare_persistent<256>());
+    GB_TRY(prepare_persistent<128>());
+    GB_TRY(prepare_persistent<64>());
     if (num_sms() <= 0) return GB_STATUS_CUDA_ERROR;
-    GB_TRY(prepare_bn<256>());
-    GB_TRY(prepare_bn<128>());
     GB_TRY(prepare_bn<64>());
     return device_status_word() ? 0 : GB_STATUS_CUDA_ERROR;
 }
@@ -446,6 +454,7 @@ static int launch_bn(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda
     return check(cudaGetLastError());
 }
 
+template <int PBN>
 static int launch_persistent(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
                              int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s, int *status)
 {
@@ -462,7 +471,7 @@ static int launch_persistent(int64_t M, int64_t N, int64_t K, const void *A, int
         uint32_t box[2] = {BK, uint32_t(PBN)};
         GB_TRY(encode_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, strides, box));
     }
-    GB_TRY(prepare_persistent());
+    GB_TRY(prepare_persistent<PBN>());
     int *st = status ? status : device_status_word();
     if (!st) return GB_STATUS_CUDA_ERROR;
     const int sms = num_sms();
@@ -470,9 +479,11 @@ static int launch_persistent(int64_t M, int64_t N, int64_t K, const void *A, int
     const int64_t nM = (M + BM - 1) / BM, nN = (N + PBN - 1) / PBN;
     if (nM * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     const int64_t grid = nM * nN < sms ? nM * nN : sms;
+    const int nk = int(K / BK);
+    const int nst = nk < PCfg<PBN>::STAGES ? nk : PCfg<PBN>::STAGES;
     LaunchScope ls(KK_GEMM_TC, s, 2.0 * M * N * K, 2.0 * (double(M) * K + double(K) * N) + 8.0 * M * N);
-    tc_gemm_bf16_persistent_kernel<<<(unsigned)grid, 320, P_SMEM_BYTES, s>>>(ta, tb, C, ldc, (int)M, (int)N, (int)K,
-                                                                            alpha, (int)nM, (int)nN, st);
+    tc_gemm_bf16_persistent_kernel<PBN><<<(unsigned)grid, 320, PCfg<PBN>::smem_for(nst), s>>>(
+        ta, tb, C, ldc, (int)M, (int)N, (int)K, alpha, (int)nM, (int)nN, nst, st);
     return check(cudaGetLastError());
 }
 
@@ -480,9 +491,10 @@ static int launch_persistent(int64_t M, int64_t N, int64_t K, const void *A, int
 // row-major, lda) and B (K x N, BF16 column-major, ldb).  K % 64 == 0,
 // lda % 8 == 0, ldb % 8 == 0, A and B 16-byte aligned; `status` is the
 // device word that records wait timeouts (nullptr = the library's own word,
-// allocated on first use).  The N-tile width is
-// the widest of 256 / 128 / 64 that still gives at least two CTAs per SM
-// of work (small leaf updates use narrow tiles to spread over the GPU).
+// allocated on first use).  The persistent kernel takes the widest N tile of
+// 256 / 128 / 64 that still gives every CTA at least two tiles (so that an
+// epilogue can overlap the next tile's MMAs); smaller updates run one CTA per
+// 128 x 64 tile with the C tile read during the mainloop.
 int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
                         int64_t ldb, float *C, int64_t ldc, float alpha, cudaStream_t s, int *status)
 {
@@ -492,10 +504,13 @@ int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t 
         return GB_STATUS_CUDA_ERROR;
     if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     const int64_t mt = (M + BM - 1) / BM;
-    if (mt * ((N + 255) / 256) >= 2 * 152)
-        return launch_persistent(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
-    if (mt * ((N + 127) / 128) >= 2 * 152)
-        return launch_bn<128>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
+    const int64_t sms = num_sms() > 0 ? num_sms() : 152;
+    if (mt * ((N + 255) / 256) >= 2 * sms)
+        return launch_persistent<256>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
+    if (mt * ((N + 127) / 128) >= 2 * sms)
+        return launch_persistent<128>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
+    if (mt * ((N + 63) / 64) >= 2 * sms)
+        return launch_persistent<64>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
     return launch_bn<64>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
 }
 
