@@ -62,6 +62,7 @@ apply_inverse_tc_kernel(const __grid_constant__ CUtensorMap tmL, int blk_row, in
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t c0 = int64_t(blockIdx.x) * TB;
+    tc::pdl_launch_dependents();
 
     if (tid == 0) {
         tc::mbar_init(&bar_tma, 1);
@@ -75,6 +76,7 @@ apply_inverse_tc_kernel(const __grid_constant__ CUtensorMap tmL, int blk_row, in
     tc::tc_fence_after();
     const uint32_t tmem = tslot;
     volatile int *ab = &abort_flag;
+    tc::pdl_wait();  // Y and its BF16 copy belong to the previous kernel until it completes
 
     if (tid == 0) {
         tc::tma_prefetch_desc(&tmL);
@@ -203,9 +205,8 @@ int launch_apply_inverse_tc(const __nv_bfloat16 *inv16, int64_t kp, int64_t b, f
     if (!st) return GB_STATUS_CUDA_ERROR;
     const int64_t grid = (ncols + TB - 1) / TB;
     LaunchScope ls(KK_DIAG, s, 3.0 * 2.0 * TB * TB * double(ncols), 4.0 * TB * TB * 2 + 10.0 * double(nr) * ncols);
-    apply_inverse_tc_kernel<<<(unsigned)grid, 128, SMEM_BYTES, s>>>(tm, int(b * TB), int(kp + b * TB), Yb, ldy,
-                                                                    Ybf_b, nr, ncols, st);
-    return check(cudaGetLastError());
+    return check(launch_pdl(apply_inverse_tc_kernel, dim3((unsigned)grid), dim3(128), SMEM_BYTES, s, tm,
+                            int(b * TB), int(kp + b * TB), Yb, ldy, Ybf_b, nr, ncols, st));
 }
 
 }  // namespace gb

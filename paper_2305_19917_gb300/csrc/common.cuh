@@ -27,6 +27,27 @@ inline int check(cudaError_t e)
 
 #define GB_CUDA(expr) GB_TRY(::gb::check(expr))
 
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous kernel of the stream is finishing (it must execute
+// griddepcontrol.wait before touching that kernel's data, and it lets the
+// next kernel do the same by executing griddepcontrol.launch_dependents).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // Canonical ("left view") form of a triangular solve.
 //
 // Every BLAS form is reduced to   Mv * Xv = alpha * Bv   where Mv is a k x k

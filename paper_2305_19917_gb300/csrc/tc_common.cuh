@@ -31,6 +31,21 @@ __device__ __forceinline__ uint64_t globaltimer()
     return t;
 }
 
+// ---- programmatic dependent launch ------------------------------------------
+// Let the next kernel of the stream start launching (its CTAs wait in
+// pdl_wait until this grid has completed) ...
+__device__ __forceinline__ void pdl_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// ... and, before touching anything the previous kernel of the stream
+// produced or consumes, wait for it to complete (a no-op when the kernel was
+// launched without the programmatic-serialisation attribute).
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---- mbarrier ----------------------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {

@@ -116,6 +116,7 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     int m_blk, n_blk;
     tc::raster_grouped(int(blockIdx.x), nMt, nNt, 8, m_blk, n_blk);
     const int nk = K / BK;
+    tc::pdl_launch_dependents();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -132,6 +133,7 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
     volatile int *ab = &abort_flag;
+    tc::pdl_wait();  // A, B and C belong to the previous kernel until it completes
 
     if (warp == 0) {
         if (lane == 0) {
@@ -259,6 +261,7 @@ tc_gemm_bf16_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = K / BK;
     const int ntiles = nMt * nNt;
+    tc::pdl_launch_dependents();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < PSTAGES; s++) {
@@ -278,6 +281,7 @@ tc_gemm_bf16_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
     volatile int *ab = &abort_flag;
+    tc::pdl_wait();  // A, B and C belong to the previous kernel until it completes
 
     if (warp == 0) {
         if (lane == 0) {
@@ -449,9 +453,8 @@ static int launch_bn(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda
     const int nk = int(K / BK);
     const int nst = nk < TileCfg<BN>::STAGES ? nk : TileCfg<BN>::STAGES;
     LaunchScope ls(KK_GEMM_TC, s, 2.0 * M * N * K, 2.0 * (double(M) * K + double(K) * N) + 8.0 * M * N);
-    tc_gemm_bf16_kernel<BN><<<grid, 192, TileCfg<BN>::smem_for(nst), s>>>(ta, tb, C, ldc, (int)M, (int)N, (int)K,
-                                                                          alpha, (int)nM, (int)nN, nst, st);
-    return check(cudaGetLastError());
+    return check(launch_pdl(tc_gemm_bf16_kernel<BN>, grid, dim3(192), TileCfg<BN>::smem_for(nst), s, ta, tb, C,
+                            ldc, (int)M, (int)N, (int)K, alpha, (int)nM, (int)nN, nst, st));
 }
 
 template <int PBN>
@@ -482,9 +485,9 @@ static int launch_persistent(int64_t M, int64_t N, int64_t K, const void *A, int
     const int nk = int(K / BK);
     const int nst = nk < PCfg<PBN>::STAGES ? nk : PCfg<PBN>::STAGES;
     LaunchScope ls(KK_GEMM_TC, s, 2.0 * M * N * K, 2.0 * (double(M) * K + double(K) * N) + 8.0 * M * N);
-    tc_gemm_bf16_persistent_kernel<PBN><<<(unsigned)grid, 320, PCfg<PBN>::smem_for(nst), s>>>(
-        ta, tb, C, ldc, (int)M, (int)N, (int)K, alpha, (int)nM, (int)nN, nst, st);
-    return check(cudaGetLastError());
+    return check(launch_pdl(tc_gemm_bf16_persistent_kernel<PBN>, dim3((unsigned)grid), dim3(320),
+                            PCfg<PBN>::smem_for(nst), s, ta, tb, C, ldc, (int)M, (int)N, (int)K, alpha, (int)nM,
+                            (int)nN, nst, st));
 }
 
 // C (M x N, FP32, column-major, ldc) = alpha*C - A*B with A (M x K, BF16
