@@ -151,7 +151,7 @@ int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
  * library image (held on every GPU that loads the library until the process
  * exits).  That bounds the problem: the padded sizes kp = 128*ceil(k/128),
  * np = 128*ceil(ncols/128) (k = order of A, ncols = right-hand sides) must
- * satisfy roughly 16 kp^2 + 26 kp np + 1050 kp + 12 np + 4 KB <= 16 MiB
+ * satisfy roughly 14 kp^2 + 34 kp np + 1550 kp + 8 np + 4 KB <= 16 MiB
  * (e.g. k = ncols = 512); larger problems return GB_STATUS_SCRATCH_TOO_SMALL
  * without touching the GPU.  The first call on a device performs a one-time
  * set-up (it looks up the array's device address), so make it before any
@@ -164,6 +164,32 @@ int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag,
                            const double *A, int64_t lda, double *B,
                            int64_t ldb, double tol, int prec, int max_iter,
                            int *iters_out, double *est_err_out, void *stream);
+
+/*
+ * gb_dtrsm_mixed_host: gb_dtrsm_mixed with A and B in HOST memory (an
+ * interface addition).  Same arguments, results and status codes, except
+ * that A (8) and B (10) are host pointers; X overwrites B on the host.  The
+ * library copies in only the referenced triangle of A (128-column panels),
+ * then B on a second stream while the kernels that need only A run, solves
+ * on `stream`, and copies X back; device buffers come from its memory pool
+ * and are released before it returns.  For the copies to overlap with
+ * computation, A and B should be page-locked (cudaHostAlloc or
+ * cudaHostRegister); pageable memory gives the same result, slower.
+ * alpha == 0 sets B = 0 on the host without reading A.  Synchronous.
+ */
+int gb_dtrsm_mixed_host(int side, int uplo, int trans, int diag,
+                        int64_t m, int64_t n, double alpha,
+                        const double *A, int64_t lda, double *B,
+                        int64_t ldb, double tol, int prec, int max_iter,
+                        int *iters_out, double *est_err_out, void *stream);
+
+/*
+ * gb_mixed_host_bytes: the bytes gb_dtrsm_mixed_host copies host -> device
+ * (return value: A's referenced triangle in 128-column panels plus B) and,
+ * in *d2h_bytes (may be NULL), device -> host (X), for the given side, uplo
+ * and sizes.  Host-only; -1 for negative sizes.
+ */
+int64_t gb_mixed_host_bytes(int side, int uplo, int64_t m, int64_t n, int64_t *d2h_bytes);
 
 /*
  * gb_mixed_history: refinement history of the last gb_dtrsm_mixed call made

@@ -53,6 +53,9 @@ _SIGS = {
                         ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
     "gb_dtrsm_mixed_noalloc": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32,
                                 ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
+    "gb_dtrsm_mixed_host": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32,
+                             ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
+    "gb_mixed_host_bytes": ([i32, i32, i64, i64, ctypes.POINTER(i64)], i64),
     "gb_trsm_batched": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "gb_batched_plan_create": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                 ctypes.POINTER(vp)], i32),
@@ -156,6 +159,23 @@ def gb_dtrsm_mixed_noalloc(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb,
     st = lib().gb_dtrsm_mixed_noalloc(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
                                       ctypes.byref(it), ctypes.byref(est), stream or None)
     return st, it.value, est.value
+
+
+def gb_dtrsm_mixed_host(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, stream=0):
+    """As gb_dtrsm_mixed with A and B in host memory (A and B are host
+    addresses; page-locked memory lets the copies overlap computation).
+    Returns (status, iters, est_err)."""
+    it, est = i32(), dbl()
+    st = lib().gb_dtrsm_mixed_host(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
+                                   ctypes.byref(it), ctypes.byref(est), stream or None)
+    return st, it.value, est.value
+
+
+def gb_mixed_host_bytes(side, uplo, m, n):
+    """(host->device, device->host) bytes of one gb_dtrsm_mixed_host call."""
+    d2h = i64()
+    h2d = lib().gb_mixed_host_bytes(side, uplo, m, n, ctypes.byref(d2h))
+    return int(h2d), int(d2h.value)
 
 
 class _BatchArgs:
@@ -308,6 +328,22 @@ def trsm_mixed(side, uplo, trans, diag, alpha, A, B, tol=1e-11, prec=0, max_iter
                                  prec, max_iter, _stream_handle(stream))
     if st < 0 or st in (STATUS_CUDA_ERROR, STATUS_TIMEOUT):
         raise GbError("gb_dtrsm_mixed", st)
+    return st, it, est
+
+
+def trsm_mixed_host(side, uplo, trans, diag, alpha, A, B, tol=1e-11, prec=0, max_iter=30, stream=None):
+    """Mixed-precision solve on torch float64 CPU tensors (column-major; pin
+    them for overlapped copies), in place on B.  Returns (status, iters,
+    est_err); raises on argument / CUDA errors."""
+    if A.device.type != "cpu" or B.device.type != "cpu":
+        raise ValueError("trsm_mixed_host takes host (CPU) tensors")
+    m, n = B.shape
+    pa, lda = _colmajor(A, "A")
+    pb, ldb = _colmajor(B, "B")
+    st, it, est = gb_dtrsm_mixed_host(side, uplo, trans, diag, m, n, float(alpha), pa, lda, pb, ldb, float(tol),
+                                      prec, max_iter, _stream_handle(stream))
+    if st < 0 or st in (STATUS_CUDA_ERROR, STATUS_TIMEOUT):
+        raise GbError("gb_dtrsm_mixed_host", st)
     return st, it, est
 
 

@@ -659,7 +659,7 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec)
 
 int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
                int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
-               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph)
+               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph, cudaEvent_t b_ready)
 {
     const int64_t k = side == GB_LEFT ? m : n;
     const int64_t ncols = side == GB_LEFT ? n : m;
@@ -720,14 +720,17 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
             prepA_kernel<<<tgrid, 256, 0, s>>>(v, kp, e_row, Abf, As, band, dg, A8, bscale);
             if ((st = check(cudaGetLastError()))) break;
         }
+        auto *binv16 = fp8 ? nullptr : reinterpret_cast<__nv_bfloat16 *>(ws + L.o_binv16);
+        if ((st = launch_invert_blocks(band, binv, binv16, kp / kBand, s))) break;
+        // everything above needs only A: the right-hand sides may still be
+        // arriving on another stream
+        if (b_ready && (st = check(cudaStreamWaitEvent(s, b_ready, 0)))) break;
         {
             LaunchScope ls(KK_CONVERT, s, 0, 16.0 * double(kp) * double(np));
             prepB_kernel<<<dim3((unsigned)(np / 64), (unsigned)(kp / 64)), 256, 0, s>>>(
                 B, ldb, side == GB_LEFT, !forward, k, ncols, alpha, R, Y, kp);
             if ((st = check(cudaGetLastError()))) break;
         }
-        auto *binv16 = fp8 ? nullptr : reinterpret_cast<__nv_bfloat16 *>(ws + L.o_binv16);
-        if ((st = launch_invert_blocks(band, binv, binv16, kp / kBand, s))) break;
         LowExec le{Y, Ybf, Abf, binv, kp, np, s, status_word};
         le.binv16 = binv16;
         le.fp8 = fp8;
@@ -806,6 +809,8 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
 }
 
 
+cudaMemPool_t mixed_pool() { return library_pool(); }
+
 int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
                      int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
                      double *est_err_out, cudaStream_t s)
@@ -816,7 +821,7 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
     char *ws = nullptr;
     GB_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&ws), L.total, pool, s));
     const int st = mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
-                              iters_out, est_err_out, s, ws, nullptr, true);
+                              iters_out, est_err_out, s, ws, nullptr, true, nullptr);
     cudaFreeAsync(ws, s);
     return st;
 }

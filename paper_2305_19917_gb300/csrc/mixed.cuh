@@ -20,11 +20,15 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec);
 // The refinement solve on a caller-provided work space `ws` (layout above,
 // 256-byte aligned), with `status_word` as the device word for wait
 // timeouts (nullptr = the library's own) and the low-precision solve either
-// replayed from a cached CUDA graph (use_graph) or launched directly.
-// Arguments are assumed valid; alpha != 0; m, n > 0.  Synchronous.
+// replayed from a cached CUDA graph (use_graph) or launched directly.  With
+// b_ready, the work that reads B waits for that event (the preparation of A
+// does not).  Arguments are assumed valid; alpha != 0; m, n > 0.  Synchronous.
 int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
                int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
-               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph);
+               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph,
+               cudaEvent_t b_ready);
+// The library's stream-ordered memory pool for work space (current device).
+cudaMemPool_t mixed_pool();
 
 // Argument checks of gb_dtrsm_mixed (0 or -i).
 int mixed_validate(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,

@@ -85,7 +85,7 @@ extern "C" int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag, i
     int *status_word = reinterpret_cast<int *>(base);
     GB_CUDA(cudaMemsetAsync(status_word, 0, sizeof(int), s));
     int st = gb::mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, iters_out,
-                            est_err_out, s, base + gb::kStatusBytes, status_word, false);
+                            est_err_out, s, base + gb::kStatusBytes, status_word, false, nullptr);
     if (st == 0 || st == GB_STATUS_NOT_CONVERGED) {
         int h = 0;
         const int c = gb::check(cudaMemcpy(&h, status_word, sizeof(int), cudaMemcpyDeviceToHost));

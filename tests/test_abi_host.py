@@ -167,3 +167,44 @@ def test_batched_argument_errors(lib):
         d[key] = bad
         assert api.gb_trsm_batched(0, [dict(base), d]) == code, key
     assert api.gb_trsm_batched(7, [base]) == -1
+
+
+# ---- host-buffer mixed entry point: argument checks and transfer accounting ----
+
+@pytest.mark.parametrize("over,expect", BAD_ARGS + [(dict(tol=-1.0), -12), (dict(prec=7), -13),
+                                                    (dict(max_iter=0), -14)])
+def test_mixed_host_invalid_arguments_rejected_without_gpu(lib, over, expect):
+    args = dict(side=0, uplo=0, trans=0, diag=0, m=8, n=10, alpha=1.0, A=0x1000, lda=8, B=0x2000, ldb=8,
+                tol=1e-11, prec=0, max_iter=30)
+    args.update(over)
+    st, it, est = api.gb_dtrsm_mixed_host(args["side"], args["uplo"], args["trans"], args["diag"], args["m"],
+                                          args["n"], args["alpha"], args["A"], args["lda"], args["B"], args["ldb"],
+                                          args["tol"], args["prec"], args["max_iter"], 0)
+    assert st == expect and it == 0 and est == 0.0
+
+
+def test_mixed_host_alpha_zero_clears_host_b_without_reading_a(lib):
+    import numpy as np
+    B = np.asfortranarray(np.full((5, 3), 7.0))
+    st, it, est = api.gb_dtrsm_mixed_host(0, 0, 0, 0, 5, 3, 0.0, 0, 5, B.ctypes.data, 5, 1e-11, 0, 30, 0)
+    assert st == 0 and np.all(B == 0.0)
+
+
+@pytest.mark.parametrize("side,uplo,m,n", [(0, 0, 300, 170), (0, 1, 300, 170), (1, 0, 64, 129),
+                                           (1, 1, 1, 1), (0, 0, 128, 7), (0, 1, 257, 2)])
+def test_mixed_host_bytes_are_triangle_panels_plus_b(lib, side, uplo, m, n):
+    k = m if side == 0 else n
+    tri = 0
+    for j0 in range(0, k, 128):   # referenced rows of each 128-column panel
+        w = min(128, k - j0)
+        tri += ((k - j0) if uplo == 0 else (j0 + w)) * w * 8
+    h2d, d2h = api.gb_mixed_host_bytes(side, uplo, m, n)
+    assert h2d == tri + m * n * 8 and d2h == m * n * 8
+    assert tri <= k * k * 8
+
+
+def test_mixed_host_copies_about_half_of_a_at_scale(lib):
+    k = 16384
+    h2d, d2h = api.gb_mixed_host_bytes(0, 0, k, k)
+    a = h2d - k * k * 8
+    assert 0.5 * k * k * 8 < a < 0.51 * k * k * 8
