@@ -48,26 +48,80 @@ struct Unit {
     T alpha;
 };
 
+
+constexpr int NBUF = 4;  // A tiles in flight per CTA
+
+// Asynchronous copy of one element (4 or 8 bytes); `in` false writes zero.
 template <typename T>
-__device__ __forceinline__ T mv_rev(const Unit<T> &u, int i, int j)
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool in)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    const int n = in ? int(sizeof(T)) : 0;
+    if (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Address of Mv'(i, j) of the forward view of unit u (index reversal for a
+// backward problem, transposition for mt).
+template <typename T>
+__device__ __forceinline__ const T *mv_addr(const Unit<T> &u, int i, int j)
 {
     const bool mt = u.flags & 1, rev = u.flags & 2;
     const int io = rev ? u.k - 1 - i : i, jo = rev ? u.k - 1 - j : j;
-    return mt ? u.A[jo + int64_t(io) * u.lda] : u.A[io + int64_t(jo) * u.lda];
+    return mt ? u.A + jo + int64_t(io) * u.lda : u.A + io + int64_t(jo) * u.lda;
 }
 
-// smem: Xs[KMAX][CW+1], tile Ts[NBB][NBB+1], inverse diagonal.
+// Tile number t of a unit's sequence: block row jb, then tiles ib = 0..jb
+// (ib < jb: gemm tasks, ib == jb: the TS task), i.e. t = jb(jb+1)/2 + ib.
+__device__ __forceinline__ void tile_of(int t, int &jb, int &ib)
+{
+    int j = int((sqrtf(8.0f * float(t) + 1.0f) - 1.0f) * 0.5f);
+    while ((j + 1) * (j + 2) / 2 <= t) j++;
+    while (j * (j + 1) / 2 > t) j--;
+    jb = j;
+    ib = t - j * (j + 1) / 2;
+}
+
+// Issue the asynchronous loads of tile t into buffer Tb (reading along A's
+// contiguous dimension): the gemm tiles in full, the TS tile on and below
+// its diagonal; everything else (and the ragged edge) reads as zero.
+template <typename T>
+__device__ __forceinline__ void load_tile(const Unit<T> &u, int t, T *Tb)
+{
+    int jb, ib;
+    tile_of(t, jb, ib);
+    const int j0 = jb * NBB, i0 = ib * NBB, k = u.k;
+    const bool mt = u.flags & 1;
+    for (int idx = threadIdx.x; idx < NBB * NBB; idx += NT) {
+        const int fast = idx % NBB, slow = idx / NBB;
+        const int rr = mt ? slow : fast, kk = mt ? fast : slow;
+        const bool in = j0 + rr < k && i0 + kk < k && (ib < jb || kk <= rr);
+        cp_async_elem(Tb + rr * (NBB + 1) + kk, in ? mv_addr(u, j0 + rr, i0 + kk) : u.A, in);
+    }
+}
+
+// smem: Xs[KMAX][LX], NBUF tiles Ts[NBB][NBB+1], inverse diagonal.
 template <typename T>
 __global__ void __launch_bounds__(NT)
 batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restrict__ ticket)
 {
     constexpr int CW = BCfg<T>::CW;
-    constexpr int LX = CW + 1;
+    // row stride of Xs: padded to 16 bytes so that a thread's PER columns
+    // load as one vector (every thread of a warp reads the same row: a
+    // broadcast)
+    constexpr int LX = CW + int(16 / sizeof(T));
     constexpr int PER = CW / 8;  // outputs per thread in the update (8 threads per row)
+    static_assert(PER * sizeof(T) == 16, "one 16-byte vector of X per thread and k");
+    constexpr int TS = NBB * (NBB + 1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);
     T *Ts = Xs + KMAX * LX;
-    T *inv = Ts + NBB * (NBB + 1);
+    T *inv = Ts + NBUF * TS;
     __shared__ int cur;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -79,76 +133,76 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
         if (t >= nunits) return;
         const Unit<T> u = units[t];
         const int k = u.k, cw = u.cw;
-        const bool mt = u.flags & 1, rev = u.flags & 2, unitd = u.flags & 4, left = u.flags & 8;
-
-        // ---- Xs = alpha * Bv' (forward view of the chunk) ------------------
-        for (int idx = tid; idx < k * CW; idx += NT) {
-            int i, c;
-            if (left) { i = idx % k; c = idx / k; }   // contiguous along i
-            else      { c = idx % CW; i = idx / CW; }  // contiguous along c
-            T v = T(0);
-            if (c < cw) {
-                const int io = rev ? k - 1 - i : i;
-                v = u.alpha * (left ? u.B[io + int64_t(c) * u.ldb] : u.B[c + int64_t(io) * u.ldb]);
-            }
-            Xs[i * LX + c] = v;
-        }
-        __syncthreads();
-
+        const bool rev = u.flags & 2, unitd = u.flags & 4, left = u.flags & 8;
         const int nblk = (k + NBB - 1) / NBB;
-        for (int jb = 0; jb < nblk; jb++) {
-            const int j0 = jb * NBB;
-            const int nr = min(NBB, k - j0);
-            // ---- gemm tasks: X_j -= Mv'(j, i) X_i for all solved blocks i ---
-            const int r = tid >> 3, cq = (tid & 7) * PER;
-            T acc[PER];
+        const int ntile = nblk * (nblk + 1) / 2;
+
+        // ---- Xs = Bv' (forward view of the chunk; alpha is applied on the
+        // way out), issued together with the first A tiles --------------------
+        // rows k .. 32*nblk-1 are zero: the ragged last block multiplies them
+        // by zero tile entries, and stale shared memory could hold a NaN
+        const int kr = nblk * NBB;
+        for (int idx = tid; idx < kr * CW; idx += NT) {
+            int i, c;
+            if (left) { i = idx % kr; c = idx / kr; }   // contiguous along i
+            else      { c = idx % CW; i = idx / CW; }   // contiguous along c
+            const int io = rev ? k - 1 - i : i;
+            const bool in = c < cw && i < k;
+            cp_async_elem(Xs + i * LX + c, in ? (left ? u.B + io + int64_t(c) * u.ldb : u.B + c + int64_t(io) * u.ldb)
+                                              : u.B,
+                          in);
+        }
+        cp_async_commit();
 #pragma unroll
-            for (int e = 0; e < PER; e++) acc[e] = T(0);
-            for (int ib = 0; ib < jb; ib++) {
+        for (int q = 0; q < NBUF - 1; q++) {
+            if (q < ntile) load_tile(u, q, Ts + q * TS);
+            cp_async_commit();
+        }
+
+        const int r = tid >> 3, cq = (tid & 7) * PER;
+        T acc[PER];
+#pragma unroll
+        for (int e = 0; e < PER; e++) acc[e] = T(0);
+        for (int tt = 0; tt < ntile; tt++) {
+            // keep NBUF - 1 tiles in flight: issue tile tt + NBUF - 1, then
+            // wait until tile tt (and the B chunk) has landed
+            if (tt + NBUF - 1 < ntile) load_tile(u, tt + NBUF - 1, Ts + ((tt + NBUF - 1) % NBUF) * TS);
+            cp_async_commit();
+            cp_async_wait<NBUF - 1>();
+            __syncthreads();
+            const T *Tb = Ts + (tt % NBUF) * TS;
+            int jb, ib;
+            tile_of(tt, jb, ib);
+            const int j0 = jb * NBB, nr = min(NBB, k - j0);
+            if (ib < jb) {
+                // gemm task: acc += Mv'(j, i) X_i
                 const int i0 = ib * NBB;
-                for (int idx = tid; idx < NBB * NBB; idx += NT) {
-                    const int fast = idx % NBB, slow = idx / NBB;
-                    // read along A's contiguous dimension
-                    int rr, kk;
-                    if (!mt) { rr = fast; kk = slow; }
-                    else     { kk = fast; rr = slow; }
-                    T v = T(0);
-                    if (rr < nr) v = mv_rev(u, j0 + rr, i0 + kk);
-                    Ts[rr * (NBB + 1) + kk] = v;
-                }
-                __syncthreads();
 #pragma unroll 8
                 for (int kk = 0; kk < NBB; kk++) {
-                    const T a = Ts[r * (NBB + 1) + kk];
+                    const T a = Tb[r * (NBB + 1) + kk];
+                    const uint4 xv = *reinterpret_cast<const uint4 *>(Xs + (i0 + kk) * LX + cq);
+                    const T *x = reinterpret_cast<const T *>(&xv);
 #pragma unroll
-                    for (int e = 0; e < PER; e++) acc[e] += a * Xs[(i0 + kk) * LX + cq + e];
+                    for (int e = 0; e < PER; e++) acc[e] += a * x[e];
                 }
-                __syncthreads();
-            }
-            if (r < nr) {
+            } else {
+                // X_j -= sum of the gemm tasks, then the TS task: the nr x nr
+                // triangle by warp-shuffle substitution
+                if (r < nr) {
 #pragma unroll
-                for (int e = 0; e < PER; e++) Xs[(j0 + r) * LX + cq + e] -= acc[e];
-            }
-            // ---- TS task: the nr x nr triangle by warp-shuffle substitution -
-            for (int idx = tid; idx < NBB * NBB; idx += NT) {
-                const int fast = idx % NBB, slow = idx / NBB;
-                int rr, kk;
-                if (!mt) { rr = fast; kk = slow; }
-                else     { kk = fast; rr = slow; }
-                T v = T(0);
-                if (rr < nr && kk < nr && kk < rr) v = mv_rev(u, j0 + rr, j0 + kk);
-                Ts[rr * (NBB + 1) + kk] = v;
-            }
-            if (tid < NBB) inv[tid] = (tid < nr && !unitd) ? T(1) / mv_rev(u, j0 + tid, j0 + tid) : T(1);
-            __syncthreads();
-            // warp w solves columns w, w+8, ... (PER columns, interleaved for ILP)
-            {
+                    for (int e = 0; e < PER; e++) Xs[(j0 + r) * LX + cq + e] -= acc[e];
+                }
+#pragma unroll
+                for (int e = 0; e < PER; e++) acc[e] = T(0);
+                if (tid < NBB) inv[tid] = (tid < nr && !unitd) ? T(1) / Tb[tid * (NBB + 1) + tid] : T(1);
+                __syncthreads();
+                // warp w solves columns w, w+8, ... (PER columns, interleaved for ILP)
                 T tv[PER];
 #pragma unroll
                 for (int e = 0; e < PER; e++) tv[e] = (lane < nr) ? Xs[(j0 + lane) * LX + warp + 8 * e] : T(0);
                 for (int kk = 0; kk < nr; kk++) {
                     const T d = inv[kk];
-                    const T lk = Ts[lane * (NBB + 1) + kk];
+                    const T lk = Tb[lane * (NBB + 1) + kk];
 #pragma unroll
                     for (int e = 0; e < PER; e++) {
                         const T x = __shfl_sync(0xffffffffu, tv[e], kk) * d;
@@ -161,17 +215,18 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
                     for (int e = 0; e < PER; e++) Xs[(j0 + lane) * LX + warp + 8 * e] = tv[e];
                 }
             }
-            __syncthreads();
+            __syncthreads();  // the buffer of tile tt is reused NBUF - 1 tiles later
         }
+        cp_async_wait<0>();
 
-        // ---- write back (undo reversal / transposition) ---------------------
+        // ---- write back alpha * X (undo reversal / transposition) -----------
         for (int idx = tid; idx < k * CW; idx += NT) {
             int i, c;
             if (left) { i = idx % k; c = idx / k; }
             else      { c = idx % CW; i = idx / CW; }
             if (c < cw) {
                 const int io = rev ? k - 1 - i : i;
-                const T v = Xs[i * LX + c];
+                const T v = u.alpha * Xs[i * LX + c];
                 if (left) u.B[io + int64_t(c) * u.ldb] = v;
                 else u.B[c + int64_t(io) * u.ldb] = v;
             }
@@ -183,7 +238,7 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
 template <typename T>
 constexpr size_t batched_smem()
 {
-    return sizeof(T) * (size_t(KMAX) * (BCfg<T>::CW + 1) + NBB * (NBB + 1) + NBB);
+    return sizeof(T) * (size_t(KMAX) * (BCfg<T>::CW + 16 / sizeof(T)) + NBUF * NBB * (NBB + 1) + NBB);
 }
 
 }  // namespace
