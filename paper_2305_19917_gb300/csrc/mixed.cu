@@ -56,6 +56,24 @@ namespace {
 constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
 constexpr int kBand = 128;     // FP32 band of diagonal 128-blocks (column-major per block)
 
+// z * 2^e as a double for |z| < 2^31 (exact: no rounding), built with 32-bit
+// integer operations (an int -> double conversion runs on the FP64 pipe,
+// which retires two operations per clock and SM); results outside the
+// normal range take the library path.
+__device__ __forceinline__ double scaled_i32_to_f64(int z, int e)
+{
+    if (z == 0) return 0.0;
+    const unsigned sign = z < 0 ? 0x80000000u : 0u;
+    const unsigned u = z < 0 ? 0u - unsigned(z) : unsigned(z);
+    const int lz = __clz(int(u));
+    const int ex = 31 - lz + e;
+    if (ex < -1022 || ex > 1023) return ldexp(double(z), e);
+    const unsigned m = (lz == 31) ? 0u : (u << (lz + 1));  // fraction bits below the leading one
+    const unsigned hi = sign | (unsigned(ex + 1023) << 20) | (m >> 12);
+    const unsigned lo = m << 20;
+    return __hiloint2double(int(hi), int(lo));
+}
+
 // Canonical forward view of the user problem (device-side description).
 struct View {
     const double *A;
@@ -323,8 +341,9 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
         z1[i] = __int2bfloat16_rn(q1);
         z2[i] = __int2bfloat16_rn(q2);
         const float d = float(N) * down;  // exact
-        if (first) x[i] = double(d);
-        else x[i] += double(d);
+        const double dd = scaled_i32_to_f64(N, f - 16);  // the same value as a double
+        if (first) x[i] = dd;
+        else x[i] += dd;
         sd = fmaf(d, d, sd);
     }
     if (first) sx = sd;
@@ -418,7 +437,7 @@ residual_apply_kernel(double *R, const long long *Tg, const int *e_row, const in
     double v = R[o] - scaled_i64_to_f64(Tg[o], e_row[i] - W + fj);
     if (i >= k_lo && i < k_hi) {
         const int z = __bfloat162int_rn(Zs[o]) * 256 + __bfloat162int_rn(Zs[np * kp + o]);
-        v = fma(-dg[i], scaled_i64_to_f64(z, fj - 16), v);
+        v = fma(-dg[i], scaled_i32_to_f64(z, fj - 16), v);
         Y[o] = f64_to_f32_rn(v);
     }
     R[o] = v;
