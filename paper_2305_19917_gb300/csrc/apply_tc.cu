@@ -10,12 +10,13 @@
 // dropped Ll Yl term and the splitting leave about 2^-16 relative error,
 // below that of the BF16 trailing updates around it.
 //
-// One CTA (4 warps) per 128-column panel.  The inverse's two terms arrive by
+// One CTA (8 warps) per 128-column panel.  The inverse's two terms arrive by
 // TMA (128-byte swizzle, K-major); the CTA reads its FP32 panel of Y, splits
 // it and writes both terms in the same swizzled K-major layout itself, then
-// one thread issues the 3 x 8 MMAs (M = N = 128, K = 16 each) and all four
-// warps drain the accumulator (warp w owns TMEM lanes 32w..32w+31 = rows),
-// storing X_b in FP32 and BF16.  The whole panel is read before any of it is
+// one thread issues the 3 x 8 MMAs (M = N = 128, K = 16 each) and all eight
+// warps drain the accumulator (warps w and w+4 share TMEM lanes
+// 32(w%4)..+31 = rows and take one half of the columns each), storing X_b
+// in FP32 and BF16.  The whole panel is read before any of it is
 // written, and CTAs own disjoint columns, so the update can be in place.
 #include <cuda_bf16.h>
 #include "common.cuh"
@@ -49,7 +50,9 @@ __device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, boo
                  : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1)
+constexpr int NTH = 256;
+
+__global__ void __launch_bounds__(NTH, 1)
 apply_inverse_tc_kernel(const __grid_constant__ CUtensorMap tmL, int blk_row, int lo_row, float *__restrict__ Y,
                         int64_t ldy, __nv_bfloat16 *__restrict__ Ybf, int nr, int64_t ncols, int *status)
 {
@@ -89,7 +92,7 @@ apply_inverse_tc_kernel(const __grid_constant__ CUtensorMap tmL, int blk_row, in
     // stage the FP32 panel: every copy of the CTA in flight at once (rows >=
     // nr and columns >= ncols read as zero; nr is a multiple of 4 or the
     // whole block, so a 16-byte piece is either all inside or all outside)
-    for (int idx = tid; idx < TB * TB / 4; idx += 128) {
+    for (int idx = tid; idx < TB * TB / 4; idx += NTH) {
         const int j = idx >> 5, k4 = (idx & 31) * 4;
         const int64_t col = c0 + j;
         const bool in = col < ncols && k4 < nr;
@@ -98,7 +101,7 @@ apply_inverse_tc_kernel(const __grid_constant__ CUtensorMap tmL, int blk_row, in
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     // split: task = (column j, 8 consecutive rows k0..k0+7)
-    for (int task = tid; task < TB * 16; task += 128) {
+    for (int task = tid; task < TB * 16; task += NTH) {
         const int j = task >> 4, k0 = (task & 15) * 8;
         const float4 a = *reinterpret_cast<const float4 *>(sP + j * TB + k0);
         const float4 b = *reinterpret_cast<const float4 *>(sP + j * TB + k0 + 4);
@@ -141,11 +144,12 @@ apply_inverse_tc_kernel(const __grid_constant__ CUtensorMap tmL, int blk_row, in
     }
     if (tc::mbar_wait(&bar_mma, 0, ab, status, tc::TC_TIMEOUT_EPILOGUE) && !*ab) {
         tc::tc_fence_after();
-        const int r = warp * 32 + lane;
+        const int q = warp & 3, half = warp >> 2;
+        const int r = q * 32 + lane;
 #pragma unroll 1
-        for (int cc = 0; cc < TB; cc += 32) {
+        for (int cc = half * (TB / 2); cc < (half + 1) * (TB / 2); cc += 32) {
             uint32_t x[32];
-            tc::tmem_ld32(tmem + (uint32_t(warp * 32) << 16) + uint32_t(cc), x);
+            tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(cc), x);
             tc::tmem_ld_wait();
             if (r < nr) {
 #pragma unroll
@@ -205,7 +209,7 @@ int launch_apply_inverse_tc(const __nv_bfloat16 *inv16, int64_t kp, int64_t b, f
     if (!st) return GB_STATUS_CUDA_ERROR;
     const int64_t grid = (ncols + TB - 1) / TB;
     LaunchScope ls(KK_DIAG, s, 3.0 * 2.0 * TB * TB * double(ncols), 4.0 * TB * TB * 2 + 10.0 * double(nr) * ncols);
-    return check(launch_pdl(apply_inverse_tc_kernel, dim3((unsigned)grid), dim3(128), SMEM_BYTES, s, tm,
+    return check(launch_pdl(apply_inverse_tc_kernel, dim3((unsigned)grid), dim3(NTH), SMEM_BYTES, s, tm,
                             int(b * TB), int(kp + b * TB), Yb, ldy, Ybf_b, nr, ncols, st));
 }
 
