@@ -151,7 +151,7 @@ int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
  * library image (held on every GPU that loads the library until the process
  * exits).  That bounds the problem: the padded sizes kp = 128*ceil(k/128),
  * np = 128*ceil(ncols/128) (k = order of A, ncols = right-hand sides) must
- * satisfy roughly 14 kp^2 + 34 kp np + 1550 kp + 8 np + 4 KB <= 16 MiB
+ * satisfy roughly 14 kp^2 + 42 kp np + 1550 kp + 16 np + 4 KB <= 16 MiB
  * (e.g. k = ncols = 512); larger problems return GB_STATUS_SCRATCH_TOO_SMALL
  * without touching the GPU.  The first call on a device performs a one-time
  * set-up (it looks up the array's device address), so make it before any

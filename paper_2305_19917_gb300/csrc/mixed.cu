@@ -54,6 +54,12 @@ int launch_apply_inverse(const float *Linv_b, float *Yb, int64_t ldy, __nv_bfloa
 namespace {
 
 constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
+// The corrections of the first kZSlots refinement steps are kept as their
+// digit slices (z_1, z_2 and the column exponents) and X = D_0 + D_1 + ... is
+// formed only when the solution is written back (in the same FP64 order as
+// X += D_t, so the result is identical); a longer refinement folds them into
+// an FP64 X once and updates X in place from then on.
+constexpr int kZSlots = 3;
 constexpr int kBand = 128;     // FP32 band of diagonal 128-blocks (column-major per block)
 
 // z * 2^e as a double for |z| < 2^31 (exact: no rounding), built with 32-bit
@@ -278,17 +284,42 @@ prepB_kernel(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64
     }
 }
 
-// B(user) = X' mapped back (only the m x n user entries).
+// X(i,j) from the digit slices of the first nz corrections: D_t = (256 z_1 +
+// z_2) 2^(f_t(j) - 16), summed as ((D_0 + D_1) + D_2) in FP64 like X += D_t.
+__device__ __forceinline__ double x_from_slots(const __nv_bfloat16 *Zs, const int *fz, int nz, int64_t kp,
+                                               int64_t np, int64_t i, int64_t j)
+{
+    const size_t kn = size_t(kp) * size_t(np), o = size_t(i) + size_t(j) * size_t(kp);
+    double x = 0.0;
+    for (int t = 0; t < nz; t++) {
+        const __nv_bfloat16 *z = Zs + size_t(t) * 2 * kn;
+        const int n = __bfloat162int_rn(z[o]) * 256 + __bfloat162int_rn(z[kn + o]);
+        const double d = scaled_i32_to_f64(n, fz[size_t(t) * np + j] - 16);
+        x = (t == 0) ? d : x + d;
+    }
+    return x;
+}
+
+// X = the sum of the kept corrections (when the refinement outgrows the slots).
+__global__ void __launch_bounds__(256)
+fold_slots_kernel(double *X, const __nv_bfloat16 *Zs, const int *fz, int nz, int64_t kp, int64_t np)
+{
+    const int64_t i = int64_t(blockIdx.y) * 256 + threadIdx.x, j = blockIdx.x;
+    if (i < kp) X[i + j * kp] = x_from_slots(Zs, fz, nz, kp, np, i, j);
+}
+
+// B(user) = X' mapped back (only the m x n user entries); X' is read from X
+// (nz == 0) or formed from the digit slices of the first nz corrections.
 __global__ void __launch_bounds__(256)
 writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t ncols, const double *X,
-                 int64_t kp)
+                 int64_t kp, int64_t np, const __nv_bfloat16 *Zs, const int *fz, int nz)
 {
     __shared__ double t[64][65];
     const int64_t i0 = int64_t(blockIdx.y) * 64, j0 = int64_t(blockIdx.x) * 64;
     const int tid = threadIdx.x;
     for (int idx = tid; idx < 64 * 64; idx += 256) {
         int li = idx & 63, lj = idx >> 6;
-        t[li][lj] = X[(i0 + li) + (j0 + lj) * kp];
+        t[li][lj] = nz ? x_from_slots(Zs, fz, nz, kp, np, i0 + li, j0 + lj) : X[(i0 + li) + (j0 + lj) * kp];
     }
     __syncthreads();
     for (int idx = tid; idx < 64 * 64; idx += 256) {
@@ -332,7 +363,7 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
     const float up = ldexpf(1.0f, 16 - f), down = ldexpf(1.0f, f - 16);
     __nv_bfloat16 *z1 = Zs + j * kp;
     __nv_bfloat16 *z2 = Zs + np * kp + j * kp;
-    double *x = X + j * kp;
+    double *x = X ? X + j * kp : nullptr;
     float sd = 0.f, sx = 0.f;
     for (int64_t i = threadIdx.x; i < kp; i += 256) {
         const int N = (be > 0) ? __float2int_rn(y[i] * up) : 0;
@@ -341,9 +372,11 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
         z1[i] = __int2bfloat16_rn(q1);
         z2[i] = __int2bfloat16_rn(q2);
         const float d = float(N) * down;  // exact
-        const double dd = scaled_i32_to_f64(N, f - 16);  // the same value as a double
-        if (first) x[i] = dd;
-        else x[i] += dd;
+        if (x) {
+            const double dd = scaled_i32_to_f64(N, f - 16);  // the same value as a double
+            if (first) x[i] = dd;
+            else x[i] += dd;
+        }
         sd = fmaf(d, d, sd);
     }
     if (first) sx = sd;
@@ -536,7 +569,12 @@ void pairs_for(double rho, double tol, int *P, int *P2)
     const double budget = target - b + 16.0;
     int p1 = int(std::floor((budget - 8.0) / 8.0));
     int p2 = int(std::floor((budget - 16.0) / 8.0));
-    if (p1 > kSlices) p1 = kSlices;
+    // the int64 sums of the residual hold 2^(W+8) per 1024-chunk, 16 chunks a
+    // launch: W = max(8 P + 8, 8 P2 + 16) <= 48 keeps them below 2^61 (this
+    // bounds the attainable residual accuracy near 2^-48 |Mv||X|: a tol much
+    // below 1e-13 is not reached and is reported as not converged)
+    if (p1 > kSlices - 1) p1 = kSlices - 1;
+    if (p2 > kSlices - 2) p2 = kSlices - 2;
     if (p1 < 1) p1 = 1;
     if (p2 > p1) p2 = p1;
     if (p2 < 0) p2 = 0;
@@ -656,9 +694,9 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec)
     L.o_x = take(kn * 8);
     L.o_y = take(kn * 4);
     L.o_ybf = take(kn * 2);
-    L.o_zs = take(kn * 4);
+    L.o_zs = take(kn * 4 * kZSlots);
     L.o_e = take(size_t(L.kp) * 4);
-    L.o_f = take(size_t(L.np) * 4);
+    L.o_f = take(size_t(L.np) * 4 * kZSlots);
     L.o_norm = take(64);
     L.o_dg = take(size_t(L.kp) * 8);
     L.o_xm = take(size_t(L.np) * 4);
@@ -760,6 +798,10 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
         LowGraph *lg = nullptr;
         if (use_graph && (st = low_graph(le, ws, &lg))) break;
         const int64_t nel = int64_t(kn);
+        __nv_bfloat16 *Zc = Zs;  // digit slot of the current correction
+        int *fc = f_col;
+        bool folded = false;
+        int nz = 0;              // corrections held in slots (0: X holds the sum)
         int Lmax = 76;
         double nx = 0, prev_rho = 0;
         for (int t = 0;; t++) {
@@ -772,12 +814,25 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
                 if ((st = low_solve(le, kp))) break;
             }
             if ((st = check(cudaMemsetAsync(norms, 0, 3 * sizeof(double), s)))) break;
+            // this step's digit slot; the first kZSlots corrections stay in
+            // their slots (X untouched), later ones fold them into X first
+            const int slot = t % kZSlots;
+            Zc = Zs + size_t(slot) * 2 * kn;
+            fc = f_col + size_t(slot) * np;
+            if (t == kZSlots) {
+                LaunchScope ls(KK_CONVERT, s, 0, (8.0 + 4.0 * kZSlots) * double(nel));
+                fold_slots_kernel<<<dim3((unsigned)np, (unsigned)((kp + 255) / 256)), 256, 0, s>>>(X, Zs, f_col, kZSlots,
+                                                                                             kp, np);
+                if ((st = check(cudaGetLastError()))) break;
+                folded = true;
+            }
             {
-                LaunchScope ls(KK_CONVERT, s, 0, 20.0 * double(nel));
-                slice_cols_kernel<<<(unsigned)np, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms,
-                                                                t == 0);
+                LaunchScope ls(KK_CONVERT, s, 0, (folded ? 24.0 : 8.0) * double(nel));
+                slice_cols_kernel<<<(unsigned)np, 256, 0, s>>>(Y, kp, np, ncols, Zc, fc, folded ? X : nullptr,
+                                                                xmax, norms, t == 0);
                 if ((st = check(cudaGetLastError()))) break;
             }
+            nz = folded ? 0 : t + 1;
             if ((st = check(cudaMemcpyAsync(h_norm, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)))) break;
             if ((st = check(cudaStreamSynchronize(s)))) break;
             const double nd = std::sqrt(h_norm[0]);
@@ -807,13 +862,13 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
             int P = kSlices, P2 = kSlices - 1;
             pairs_for(t == 0 ? 1.0 : h_norm[2], tol, &P, &P2);
             Lmax = P * 10 + P2;  // recorded in the history as 10*P + P2
-            if ((st = residual_update(R, Tg, As, Zs, e_row, f_col, dg, Y, kp, np, P, P2, s, status_word))) break;
+            if ((st = residual_update(R, Tg, As, Zc, e_row, fc, dg, Y, kp, np, P, P2, s, status_word))) break;
         }
         if (st) break;
         {
             LaunchScope ls(KK_CONVERT, s, 0, 16.0 * double(k) * double(ncols));
             writeback_kernel<<<dim3((unsigned)(np / 64), (unsigned)(kp / 64)), 256, 0, s>>>(
-                B, ldb, side == GB_LEFT, !forward, k, ncols, X, kp);
+                B, ldb, side == GB_LEFT, !forward, k, ncols, X, kp, np, Zs, f_col, nz);
             if ((st = check(cudaGetLastError()))) break;
         }
     } while (0);

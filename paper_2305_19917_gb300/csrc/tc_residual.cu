@@ -265,6 +265,8 @@ int launch_tc_residual(long long *Tg, int64_t ldr, const void *As, const void *Z
         P2 > P)
         return GB_STATUS_CUDA_ERROR;
     const int W = residual_weight(P, P2);
+    // |T| <= 16 chunks x 1.01 x 2^(24 + W - 16) must stay below 2^63
+    if (W > 50) return GB_STATUS_CUDA_ERROR;
     if (kp > 0x7fffffffLL || np > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     CUtensorMap ta, tz;
     {

@@ -103,3 +103,21 @@ def test_mixed_fp8_block_scaled_updates(side, uplo, trans, diag):
     torch.cuda.synchronize()
     assert st == 0 and it <= 40, (st, it, est, api.gb_mixed_history())
     assert fwd_err(Bd.cpu().numpy(), Xo) <= 1e-10
+
+
+@pytest.mark.parametrize("max_iter", [3, 5])
+def test_long_refinement_folds_kept_corrections(max_iter):
+    """tol = 0 runs max_iter refinement steps: beyond the corrections kept as
+    digit slices the library folds them into X; the solution stays right."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    side, uplo, trans, diag, m, n, alpha = 0, 1, 1, 0, 300, 77, -1.25
+    A, B = inputs.make_problem(side, uplo, trans, diag, m, n, seed=21)
+    Ad = api.to_device_colmajor(A, torch.float64)
+    Bd = api.to_device_colmajor(B, torch.float64)
+    st, it, est = api.trsm_mixed(side, uplo, trans, diag, alpha, Ad, Bd, tol=0.0, max_iter=max_iter)
+    torch.cuda.synchronize()
+    assert it == max_iter and st in (0, api.STATUS_NOT_CONVERGED)
+    Xo = oracle.dtrsm(side, uplo, trans, diag, alpha, A, B)
+    X = Bd.cpu().numpy()
+    assert np.linalg.norm(X - Xo) <= 1e-10 * np.linalg.norm(Xo)
