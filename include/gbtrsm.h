@@ -134,9 +134,13 @@ enum { GB_PREC_BF16 = 0, GB_PREC_FP8 = 1 };
  *  16 est_err_out host, optional: last ||D||_F / ||X||_F
  *  17 stream
  * Returns 0 when converged, GB_STATUS_NOT_CONVERGED (X = last iterate) when
- * max_iter was reached first.  Synchronous: returns after the solve is
- * complete.  Work space (about 8 k^2 + 28 k n bytes, k and n rounded up to
- * multiples of 128) comes from a library-owned stream-ordered pool.
+ * max_iter was reached first.  The residual's exact digit sums bound the
+ * attainable accuracy near 2^-48 |op(A)||X| (a tol much below 1e-13 is not
+ * reached), and the low-precision solve needs alpha*B and X within the FP32
+ * range (about 3.4e38); beyond either the call reports not converged.
+ * Synchronous: returns after the solve is complete.  Work space (about
+ * 14 k^2 + 42 k n bytes, k and n rounded up to multiples of 128) comes from a
+ * library-owned stream-ordered pool.
  */
 int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
                    int64_t n, double alpha, const double *A, int64_t lda,

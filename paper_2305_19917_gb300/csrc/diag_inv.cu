@@ -1,11 +1,13 @@
 // Diagonal-block step of the mixed-precision low-precision solve, done by
 // inversion: each 128 x 128 lower-triangular diagonal block L_b is inverted
-// once per solve (FP32, one CTA per block, triangle in shared memory), and
-// every TS task of the refinement then applies X_b = L_b^-1 Y_b as a
-// register-tiled FP32 triangular matrix product on CUDA cores, writing the
-// FP32 result and its BF16 copy (the operand of the tensor-core updates).
-// This turns the serial substitution on the critical path of the recursive
-// model (Section V-A, the TS(i) leaves) into a fully parallel product.
+// once per solve (FP32, one CTA per block, triangle in shared memory) into
+// FP32 strips and a two-term BF16 split, and every TS task of the
+// refinement then applies X_b = L_b^-1 Y_b as a product: on the tensor cores
+// from the BF16 split (apply_tc.cu), or, in the FP8 form, here as a
+// register-tiled FP32 triangular product on the CUDA cores that also writes
+// the FP8 copy with its block scales.  This turns the serial substitution on
+// the critical path of the recursive model (Section V-A, the TS(i) leaves)
+// into a fully parallel product.
 //
 // Storage ("band"): block b occupies band[(b*128 + c)*128 + i] = L_b(i, c),
 // i.e. each block column-major with leading dimension 128.  The inverses use
@@ -247,8 +249,6 @@ int diag_inv_prepare()
     if (!done) {
         GB_CUDA(cudaFuncSetAttribute(invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)INV_SMEM));
-        GB_CUDA(cudaFuncSetAttribute(apply_inverse_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)apply_smem(AC)));
         GB_CUDA(cudaFuncSetAttribute(apply_inverse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)apply_smem(AC)));
         done = true;
@@ -268,24 +268,10 @@ int launch_invert_blocks(const float *band, float *inv, __nv_bfloat16 *inv16, in
     return check(cudaGetLastError());
 }
 
-// The TS task of one block: Y_b = Linv_b Y_b (+ BF16 copy).
-int launch_apply_inverse(const float *Linv_b, float *Yb, int64_t ldy, __nv_bfloat16 *Ybf_b, int nr, int64_t ncols,
-                         cudaStream_t s)
-{
-    if (nr <= 0 || ncols <= 0) return 0;
-    if (nr > NBI) return GB_STATUS_CUDA_ERROR;
-    GB_TRY(diag_inv_prepare());
-    if (ldy % 4 || (reinterpret_cast<uintptr_t>(Yb) & 15) || (reinterpret_cast<uintptr_t>(Ybf_b) & 7))
-        return GB_STATUS_CUDA_ERROR;
-    const int64_t grid = (ncols + AC - 1) / AC;
-    LaunchScope ls(KK_DIAG, s, double(nr) * nr * ncols, 4.0 * (double(nr) * nr + 2.0 * nr * ncols) + 2.0 * nr * ncols);
-    apply_inverse_kernel<false><<<(unsigned)grid, 4 * AC, apply_smem(AC), s>>>(Linv_b, Yb, ldy, Ybf_b, nr, ncols,
-                                                                                nullptr, nullptr);
-    return check(cudaGetLastError());
-}
-
-// As above, emitting the FP8 copy Y8_b (same layout) and the block scales
-// s8_b[j] of the 128 x 64 blocks j = 0, 1, ... of this row block.
+// The TS task of one block of the FP8 form: Y_b = Linv_b Y_b in FP32 on the
+// CUDA cores, plus the FP8 copy Y8_b (same layout) and the block scales
+// s8_b[j] of the 128 x 64 blocks j = 0, 1, ... of this row block (the BF16
+// form applies the inverse on the tensor cores, apply_tc.cu).
 int launch_apply_inverse_fp8(const float *Linv_b, float *Yb, int64_t ldy, uint8_t *Y8_b, float *s8_b, int nr,
                              int64_t ncols, cudaStream_t s)
 {

@@ -48,9 +48,6 @@ int launch_invert_blocks(const float *band, float *inv, __nv_bfloat16 *inv16, in
 int apply_tc_prepare();
 int launch_apply_inverse_tc(const __nv_bfloat16 *inv16, int64_t kp, int64_t b, float *Yb, int64_t ldy,
                             __nv_bfloat16 *Ybf_b, int nr, int64_t ncols, cudaStream_t s, int *status);
-int launch_apply_inverse(const float *Linv_b, float *Yb, int64_t ldy, __nv_bfloat16 *Ybf_b, int nr, int64_t ncols,
-                         cudaStream_t s);
-
 namespace {
 
 constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
@@ -530,11 +527,9 @@ struct LowExec {
         if (fp8)
             status = launch_apply_inverse_fp8(binv + b0 * kBand, Y + b0, kp, Y8 + b0, sY + (b0 / 128) * (np / 64),
                                               (int)nr, np, s);
-        else if (binv16)
+        else
             status = launch_apply_inverse_tc(binv16, kp, b0 / kBand, Y + b0, kp, Ybf + b0, (int)nr, np, s,
                                              status_word);
-        else
-            status = launch_apply_inverse(binv + b0 * kBand, Y + b0, kp, Ybf + b0, (int)nr, np, s);
     }
     void gemm(int64_t ci0, int64_t M, int64_t ak0, int64_t K, float a)
     {

@@ -121,3 +121,23 @@ def test_long_refinement_folds_kept_corrections(max_iter):
     Xo = oracle.dtrsm(side, uplo, trans, diag, alpha, A, B)
     X = Bd.cpu().numpy()
     assert np.linalg.norm(X - Xo) <= 1e-10 * np.linalg.norm(Xo)
+
+
+def test_out_of_fp32_range_is_reported_not_silent():
+    """The low-precision solve works in FP32/BF16: right-hand sides beyond the
+    FP32 range cannot be refined, and the call says so (status not converged),
+    instead of returning a wrong X as if it had converged."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    A, B = inputs.make_problem(0, 0, 0, 0, 256, 16, seed=31)
+    Ad = api.to_device_colmajor(A, torch.float64)
+    Bd = api.to_device_colmajor(B * 1e300, torch.float64)
+    st, it, est = api.trsm_mixed(0, 0, 0, 0, 1.0, Ad, Bd, max_iter=4)
+    torch.cuda.synchronize()
+    assert st == api.STATUS_NOT_CONVERGED
+    # a right-hand side scaled within the FP32 range converges as usual
+    Bd = api.to_device_colmajor(B * 1e30, torch.float64)
+    st, it, est = api.trsm_mixed(0, 0, 0, 0, 1.0, Ad, Bd)
+    torch.cuda.synchronize()
+    Xo = oracle.dtrsm(0, 0, 0, 0, 1.0, A, B * 1e30)
+    assert st == 0 and np.linalg.norm(Bd.cpu().numpy() - Xo) <= 1e-10 * np.linalg.norm(Xo)
