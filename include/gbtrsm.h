@@ -54,8 +54,12 @@ enum {
     GB_STATUS_CUDA_ERROR = 2,    /* a CUDA call failed; see gb_last_cuda_error */
     GB_STATUS_TIMEOUT = 3,       /* a device-side wait hit its iteration cap */
     GB_STATUS_NO_MODEL = 4,      /* no cost model loaded where one is needed */
-    GB_STATUS_SCRATCH_TOO_SMALL = 5 /* problem exceeds the fixed scratch of
-                                       gb_dtrsm_mixed_noalloc              */
+    GB_STATUS_SCRATCH_TOO_SMALL = 5, /* problem exceeds the fixed scratch of
+                                        gb_dtrsm_mixed_noalloc             */
+    GB_STATUS_RANGE = 6          /* mixed path: alpha*B, a residual or a
+                                    correction left the FP32 range of the
+                                    low-precision solve (B is unchanged;
+                                    use the FP64 path)                     */
 };
 
 /* Decomposition drivers (the paper's three computation models). */
@@ -137,7 +141,8 @@ enum { GB_PREC_BF16 = 0, GB_PREC_FP8 = 1 };
  * max_iter was reached first.  The residual's exact digit sums bound the
  * attainable accuracy near 2^-48 |op(A)||X| (a tol much below 1e-13 is not
  * reached), and the low-precision solve needs alpha*B and X within the FP32
- * range (about 3.4e38); beyond either the call reports not converged.
+ * range (about 3.4e38): values beyond it (or non-finite ones) return
+ * GB_STATUS_RANGE with B unchanged.
  * Synchronous: returns after the solve is complete.  Work space (about
  * 14 k^2 + 42 k n bytes, k and n rounded up to multiples of 128) comes from a
  * library-owned stream-ordered pool.

@@ -20,6 +20,7 @@ NONUNIT, UNIT = 0, 1
 DRIVER_BLOCKED, DRIVER_RECURSIVE, DRIVER_ITERATIVE, DRIVER_AUTO = 0, 1, 2, -1
 STATUS_OK, STATUS_NOT_CONVERGED, STATUS_CUDA_ERROR, STATUS_TIMEOUT, STATUS_NO_MODEL = 0, 1, 2, 3, 4
 STATUS_SCRATCH_TOO_SMALL = 5
+STATUS_RANGE = 6
 
 LIB_PATH = _build.LIB
 

@@ -156,6 +156,7 @@ const char *gb_status_string(int status)
     case GB_STATUS_TIMEOUT: return "device-side wait exceeded its iteration limit";
     case GB_STATUS_NO_MODEL: return "no cost model loaded";
     case GB_STATUS_SCRATCH_TOO_SMALL: return "problem too large for the fixed no-allocation scratch";
+    case GB_STATUS_RANGE: return "operands outside the FP32 range of the low-precision solve";
     default: return "unknown status";
     }
 }

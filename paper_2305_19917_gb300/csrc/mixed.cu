@@ -338,7 +338,9 @@ writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t
 // FP32, added in FP64).
 // Accumulates sum D~^2 into norms[0] (FP32 partial sums), and, on the first
 // call, sum X^2 into norms[1] and the column maxima of |X| into xmax; the
-// largest column ratio max|D~| / max|X| goes to norms[2] (as bits).
+// largest column ratio max|D~| / max|X| goes to norms[2] (as bits); a column
+// whose maximum is not a finite FP32 value (the low-precision solve left
+// the FP32 range, or the data are not finite) counts into norms[3].
 __global__ void __launch_bounds__(256)
 slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bfloat16 *Zs, int *f_col,
                   double *X, float *xmax, double *norms, int first)
@@ -348,10 +350,15 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
     __shared__ float red[8];
     __shared__ float redd[2][8];
     float mx = 0.f;
-    for (int64_t i = threadIdx.x; i < kp; i += 256) mx = fmaxf(mx, fabsf(y[i]));
+    int bad = 0;  // a value that is not a finite FP32 number (fmaxf would skip a NaN)
+    for (int64_t i = threadIdx.x; i < kp; i += 256) {
+        const float a = fabsf(y[i]);
+        mx = fmaxf(mx, a);
+        bad |= !(a <= 3.4028235e38f);
+    }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
+    bad = __syncthreads_or(bad);
     mx = 0.f;
     for (int w = 0; w < 8; w++) mx = fmaxf(mx, red[w]);
     const int be = int((__float_as_uint(mx) >> 23) & 0xFF);
@@ -386,6 +393,7 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
         redd[1][threadIdx.x >> 5] = sx;
     }
     __syncthreads();
+    if (threadIdx.x == 0 && j < ncols && bad) atomicAdd(&norms[3], 1.0);
     if (threadIdx.x == 0 && j < ncols) {
         float a = 0.f, b = 0.f;
         for (int w = 0; w < 8; w++) {
@@ -749,7 +757,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
     auto *xmax = reinterpret_cast<float *>(ws + o_xm);
 
     int st = 0;
-    double h_norm[3] = {0, 0, 0};
+    double h_norm[4] = {0, 0, 0, 0};
     int iters = 0;
     double est = 0;
     do {
@@ -808,7 +816,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
                 le.status = 0;
                 if ((st = low_solve(le, kp))) break;
             }
-            if ((st = check(cudaMemsetAsync(norms, 0, 3 * sizeof(double), s)))) break;
+            if ((st = check(cudaMemsetAsync(norms, 0, 4 * sizeof(double), s)))) break;
             // this step's digit slot; the first kZSlots corrections stay in
             // their slots (X untouched), later ones fold them into X first
             const int slot = t % kZSlots;
@@ -828,8 +836,12 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
                 if ((st = check(cudaGetLastError()))) break;
             }
             nz = folded ? 0 : t + 1;
-            if ((st = check(cudaMemcpyAsync(h_norm, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)))) break;
+            if ((st = check(cudaMemcpyAsync(h_norm, norms, 4 * sizeof(double), cudaMemcpyDeviceToHost, s)))) break;
             if ((st = check(cudaStreamSynchronize(s)))) break;
+            if (h_norm[3] != 0.0) {  // out of the low-precision range: B is left as it was
+                st = GB_STATUS_RANGE;
+                break;
+            }
             const double nd = std::sqrt(h_norm[0]);
             if (t == 0) nx = std::sqrt(h_norm[1]);
             const double rho = nx > 0 ? nd / nx : 0.0;

@@ -44,6 +44,7 @@ def test_version_and_status_strings(lib):
     assert api.gb_status_string(0) == "success"
     assert "argument" in api.gb_status_string(-3)
     assert "CUDA" in api.gb_status_string(api.STATUS_CUDA_ERROR)
+    assert "range" in api.gb_status_string(api.STATUS_RANGE)
     assert api.gb_last_cuda_error() == 0
 
 

@@ -125,16 +125,21 @@ def test_long_refinement_folds_kept_corrections(max_iter):
 
 def test_out_of_fp32_range_is_reported_not_silent():
     """The low-precision solve works in FP32/BF16: right-hand sides beyond the
-    FP32 range cannot be refined, and the call says so (status not converged),
-    instead of returning a wrong X as if it had converged."""
+    FP32 range (or not finite) cannot be refined, and the call says so with
+    GB_STATUS_RANGE and leaves B as it was, instead of returning a wrong X as
+    if it had converged."""
     import torch
     from paper_2305_19917_gb300 import api
     A, B = inputs.make_problem(0, 0, 0, 0, 256, 16, seed=31)
     Ad = api.to_device_colmajor(A, torch.float64)
-    Bd = api.to_device_colmajor(B * 1e300, torch.float64)
-    st, it, est = api.trsm_mixed(0, 0, 0, 0, 1.0, Ad, Bd, max_iter=4)
-    torch.cuda.synchronize()
-    assert st == api.STATUS_NOT_CONVERGED
+    for bad in (B * 1e300, np.where(np.arange(16) == 5, np.nan, B)):
+        Bd = api.to_device_colmajor(bad, torch.float64)
+        st, it, est = api.gb_dtrsm_mixed(0, 0, 0, 0, 256, 16, 1.0, Ad.data_ptr(), 256, Bd.data_ptr(), 256, 1e-11,
+                                         api.PREC_BF16, 4, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert st == api.STATUS_RANGE
+        np.testing.assert_array_equal(Bd.cpu().numpy(), bad)
+    assert "range" in api.gb_status_string(api.STATUS_RANGE)
     # a right-hand side scaled within the FP32 range converges as usual
     Bd = api.to_device_colmajor(B * 1e30, torch.float64)
     st, it, est = api.trsm_mixed(0, 0, 0, 0, 1.0, Ad, Bd)
