@@ -46,6 +46,8 @@ int launch_apply_inverse_fp8(const float *Linv_b, float *Yb, int64_t ldy, uint8_
 int diag_inv_prepare();
 int launch_invert_blocks(const float *band, float *inv, __nv_bfloat16 *inv16, int64_t nblocks, cudaStream_t s);
 int apply_tc_prepare();
+int launch_leaf_step_tc(const __nv_bfloat16 *Abf, const __nv_bfloat16 *inv16, int64_t kp, int64_t np, int64_t b0,
+                        int64_t s0, float *Y, __nv_bfloat16 *Ybf, cudaStream_t s, int *status);
 int launch_apply_inverse_tc(const __nv_bfloat16 *inv16, int64_t kp, int64_t b, float *Yb, int64_t ldy,
                             __nv_bfloat16 *Ybf_b, int nr, int64_t ncols, cudaStream_t s, int *status);
 namespace {
@@ -58,6 +60,7 @@ constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
 // an FP64 X once and updates X in place from then on.
 constexpr int kZSlots = 3;
 constexpr int kBand = 128;     // FP32 band of diagonal 128-blocks (column-major per block)
+constexpr int kLeaf = 1024;    // leaf order of the BF16 low-precision solve (8 fused leaf steps)
 
 // z * 2^e as a double for |z| < 2^31 (exact: no rounding), built with 32-bit
 // integer operations (an int -> double conversion runs on the FP64 pipe,
@@ -527,17 +530,21 @@ struct LowExec {
     void ts(int64_t b0, int64_t nr, float a)
     {
         if (status) return;
+        if (!fp8) {
+            // BF16 form: a leaf of up to kLeaf rows, left-looking: each
+            // 128-row block takes its update from the solved blocks of the
+            // leaf and its TS task in one fused kernel
+            for (int64_t blk = b0; blk < b0 + nr && !status; blk += kBand)
+                status = launch_leaf_step_tc(Abf, binv16, kp, np, blk, b0, Y, Ybf, s, status_word);
+            return;
+        }
         if (nr > kBand) {
             drive_blocked(*this, b0, b0 + nr, (int64_t)kBand, a, true);
             return;
         }
         // TS task: X_b = L_b^-1 Y_b with the precomputed inverse of the block
-        if (fp8)
-            status = launch_apply_inverse_fp8(binv + b0 * kBand, Y + b0, kp, Y8 + b0, sY + (b0 / 128) * (np / 64),
-                                              (int)nr, np, s);
-        else
-            status = launch_apply_inverse_tc(binv16, kp, b0 / kBand, Y + b0, kp, Ybf + b0, (int)nr, np, s,
-                                             status_word);
+        status = launch_apply_inverse_fp8(binv + b0 * kBand, Y + b0, kp, Y8 + b0, sY + (b0 / 128) * (np / 64),
+                                          (int)nr, np, s);
     }
     void gemm(int64_t ci0, int64_t M, int64_t ak0, int64_t K, float a)
     {
@@ -552,10 +559,11 @@ struct LowExec {
     }
 };
 
-// Recursive model (Section V-A) down to TS tasks of kBand rows.
+// Recursive model (Section V-A) down to leaves of kLeaf rows (BF16 form:
+// solved left-looking by fused leaf steps) or kBand rows (FP8 form).
 int low_solve(LowExec &e, int64_t kp)
 {
-    drive_recursive(e, 0, kp, 24, (int64_t)kBand, 1.0f, true);
+    drive_recursive(e, 0, kp, 24, (int64_t)(e.fp8 ? kBand : kLeaf), 1.0f, true);
     return e.status;
 }
 
