@@ -316,6 +316,12 @@ def run_ours(args):
     else:
         A_e = api.colmajor_empty(m, m, torch.float64)
         h2d, d2h = (m * m + m * n) * 8, m * n * 8
+    if mixed:
+        # one untimed call: the host entry point solves in column blocks, whose
+        # low-precision solve graph is captured on first use
+        B_pin.copy_(B_host0)
+        api.trsm_mixed_host(side, uplo, trans, diag, alpha, A_pin, B_pin, tol=tol, prec=prec, max_iter=max_iter,
+                            stream=stream)
     for _ in range(max(1, min(args.steps, 2))):
         B_pin.copy_(B_host0)  # fresh right-hand sides (host copy, not timed)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -338,8 +344,11 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_t = float(t.item())
     if mixed:
-        # the host solution agrees with the device-resident one
-        acc["e2e_max_abs_diff_vs_device"] = float((B_pin[:, cols] - B[:, cols].cpu()).abs().max()) if acc else None
+        # the host solution's own error, and its distance from the device-resident one
+        if acc:
+            Xe = B_pin[:, cols].numpy()
+            acc["e2e_fwd_err_sampled"] = float(np.linalg.norm(Xe - Xo) / np.linalg.norm(Xo))
+            acc["e2e_max_abs_diff_vs_device"] = float(np.abs(Xe - Xs).max())
     del A_pin, B_pin
 
     # ---- plain FP64 on the same GPU, same workload (the comparison) ----

@@ -1,23 +1,16 @@
-// TS task of the mixed-precision low-precision solve on the tensor cores:
+// Leaf step of the mixed-precision low-precision solve on the tensor cores.
+// Each 128-row block b of a leaf (the TS(i) leaves of Section V-A, solved
+// left-looking inside the leaf) takes
 //
-//     X_b = L_b^-1 Y_b        (128 rows, in place on the FP32 Y, plus its BF16 copy)
+//     Y_b -= L(b, s0:b0) X(s0:b0)        (BF16 products, FP32 in tensor memory)
+//     X_b  = L_b^-1 Y_b                  (precomputed 128 x 128 inverse)
 //
-// with the precomputed inverse of the 128 x 128 diagonal block (Section V-A's
-// TS(i) leaves turned into a product).  A plain BF16 product would add a
-// 2^-9 relative error to every block solve; instead both factors are split
-// into two BF16 terms, L^-1 = Lh + Ll and Y = Yh + Yl, and the three
-// products Lh Yh + Lh Yl + Ll Yh accumulate in FP32 in tensor memory: the
-// dropped Ll Yl term and the splitting leave about 2^-16 relative error,
-// below that of the BF16 trailing updates around it.
-//
-// One CTA (8 warps) per 128-column panel.  The inverse's two terms arrive by
-// TMA (128-byte swizzle, K-major); the CTA reads its FP32 panel of Y, splits
-// it and writes both terms in the same swizzled K-major layout itself, then
-// one thread issues the 3 x 8 MMAs (M = N = 128, K = 16 each) and all eight
-// warps drain the accumulator (warps w and w+4 share TMEM lanes
-// 32(w%4)..+31 = rows and take one half of the columns each), storing X_b
-// in FP32 and BF16.  The whole panel is read before any of it is
-// written, and CTAs own disjoint columns, so the update can be in place.
+// in one kernel, in place on the FP32 Y and its BF16 copy.  A plain BF16
+// product with the inverse would add a 2^-9 relative error to every block
+// solve; instead both factors are split into two BF16 terms, L^-1 = Lh + Ll
+// and Y = Yh + Yl, and the three products Lh Yh + Lh Yl + Ll Yh accumulate
+// in FP32: the dropped Ll Yl term and the splitting leave about 2^-16
+// relative error, below that of the BF16 trailing updates around it.
 #include <cuda_bf16.h>
 #include "common.cuh"
 #include "tc_common.cuh"
@@ -32,7 +25,6 @@ constexpr int TB = 128;                    // rows of the block = K = panel widt
 constexpr uint32_t HALF_BYTES = TB * 128;  // 128 rows x 64 BF16 (one 128-byte swizzle column)
 constexpr uint32_t OP_BYTES = 2 * HALF_BYTES;
 constexpr uint32_t PANEL_BYTES = TB * TB * 4;  // FP32 staging of the panel, [column][row]
-constexpr size_t SMEM_BYTES = 1024 + 4 * size_t(OP_BYTES) + PANEL_BYTES + 256;
 
 // Byte offset of element (row r, k) of a K-major BF16 operand with K = 128
 // stored as two 64-wide halves of 128-byte rows in the 128-byte swizzle
@@ -51,126 +43,6 @@ __device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, boo
 }
 
 constexpr int NTH = 256;
-
-__global__ void __launch_bounds__(NTH, 1)
-apply_inverse_tc_kernel(const __grid_constant__ CUtensorMap tmL, int blk_row, int lo_row, float *__restrict__ Y,
-                        int64_t ldy, __nv_bfloat16 *__restrict__ Ybf, int nr, int64_t ncols, int *status)
-{
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sLh = base, *sLl = base + OP_BYTES, *sYh = base + 2 * OP_BYTES, *sYl = base + 3 * OP_BYTES;
-    float *sP = reinterpret_cast<float *>(base + 4 * OP_BYTES);  // sP[j*128 + k] = Y(k, c0+j)
-    __shared__ uint64_t bar_tma, bar_mma;
-    __shared__ uint32_t tslot;
-    __shared__ int abort_flag;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t c0 = int64_t(blockIdx.x) * TB;
-    tc::pdl_launch_dependents();
-
-    if (tid == 0) {
-        tc::mbar_init(&bar_tma, 1);
-        tc::mbar_init(&bar_mma, 1);
-        abort_flag = 0;
-        tc::fence_barrier_init();
-    }
-    if (warp == 0) tc::tmem_alloc(&tslot, TB);
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-    const uint32_t tmem = tslot;
-    volatile int *ab = &abort_flag;
-    tc::pdl_wait();  // Y and its BF16 copy belong to the previous kernel until it completes
-
-    if (tid == 0) {
-        tc::tma_prefetch_desc(&tmL);
-        tc::mbar_arrive_expect_tx(&bar_tma, 2 * OP_BYTES);
-        tc::tma_load_2d(&tmL, &bar_tma, sLh, 0, blk_row);
-        tc::tma_load_2d(&tmL, &bar_tma, sLh + HALF_BYTES, 64, blk_row);
-        tc::tma_load_2d(&tmL, &bar_tma, sLl, 0, lo_row);
-        tc::tma_load_2d(&tmL, &bar_tma, sLl + HALF_BYTES, 64, lo_row);
-    }
-    // stage the FP32 panel: every copy of the CTA in flight at once (rows >=
-    // nr and columns >= ncols read as zero; nr is a multiple of 4 or the
-    // whole block, so a 16-byte piece is either all inside or all outside)
-    for (int idx = tid; idx < TB * TB / 4; idx += NTH) {
-        const int j = idx >> 5, k4 = (idx & 31) * 4;
-        const int64_t col = c0 + j;
-        const bool in = col < ncols && k4 < nr;
-        cp_async16_zfill(sP + j * TB + k4, in ? Y + k4 + col * ldy : Y, in);
-    }
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-    // split: task = (column j, 8 consecutive rows k0..k0+7)
-    for (int task = tid; task < TB * 16; task += NTH) {
-        const int j = task >> 4, k0 = (task & 15) * 8;
-        const float4 a = *reinterpret_cast<const float4 *>(sP + j * TB + k0);
-        const float4 b = *reinterpret_cast<const float4 *>(sP + j * TB + k0 + 4);
-        const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v[e], v[e + 1]);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(v[e] - __low2float(h), v[e + 1] - __high2float(h));
-            hw[e / 2] = *reinterpret_cast<const uint32_t *>(&h);
-            lw[e / 2] = *reinterpret_cast<const uint32_t *>(&l);
-        }
-        const uint32_t off = sw128_off(j, k0);
-        *reinterpret_cast<uint4 *>(sYh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4 *>(sYl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-    }
-    // the MMAs read shared memory through the async proxy
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-
-    if (tid == 0) {
-        if (tc::mbar_wait(&bar_tma, 0, ab, status, tc::TC_TIMEOUT_MMA)) {
-            tc::tc_fence_after();
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(TB, TB);
-            const uint8_t *As[3] = {sLh, sLh, sLl};
-            const uint8_t *Bs[3] = {sYh, sYl, sYh};
-            uint32_t acc = 0;
-#pragma unroll
-            for (int pr = 0; pr < 3; pr++) {
-                const uint32_t a0 = tc::smem_u32(As[pr]), b0 = tc::smem_u32(Bs[pr]);
-#pragma unroll
-                for (int kk = 0; kk < TB / 16; kk++) {
-                    const uint32_t o = uint32_t(kk >> 2) * HALF_BYTES + uint32_t(kk & 3) * 32u;
-                    tc::mma_f16(tmem, tc::desc_kmajor_sw128(a0 + o), tc::desc_kmajor_sw128(b0 + o), idesc, acc);
-                    acc = 1;
-                }
-            }
-        }
-        tc::mma_commit(&bar_mma);
-    }
-    if (tc::mbar_wait(&bar_mma, 0, ab, status, tc::TC_TIMEOUT_EPILOGUE) && !*ab) {
-        tc::tc_fence_after();
-        const int q = warp & 3, half = warp >> 2;
-        const int r = q * 32 + lane;
-#pragma unroll 1
-        for (int cc = half * (TB / 2); cc < (half + 1) * (TB / 2); cc += 32) {
-            uint32_t x[32];
-            tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(cc), x);
-            tc::tmem_ld_wait();
-            if (r < nr) {
-#pragma unroll
-                for (int e = 0; e < 32; e++) {
-                    const int64_t col = c0 + cc + e;
-                    if (col < ncols) {
-                        const float val = __uint_as_float(x[e]);
-                        Y[r + col * ldy] = val;
-                        Ybf[r + col * ldy] = __float2bfloat16_rn(val);
-                    }
-                }
-            }
-        }
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, TB);
-    }
-}
 
 // Left-looking leaf step: for the 128-row block at b0 of a leaf that starts
 // at s0 (K = b0 - s0 rows of that leaf already solved),
@@ -361,8 +233,6 @@ int apply_tc_prepare()
 {
     static bool attr = false;
     if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(apply_inverse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES));
         GB_CUDA(cudaFuncSetAttribute(leaf_step_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)LEAF_SMEM));
         attr = true;
@@ -370,43 +240,12 @@ int apply_tc_prepare()
     return device_status_word() ? 0 : GB_STATUS_CUDA_ERROR;
 }
 
-// X_b = L_b^-1 Y_b for diagonal block b (rows b*128 .. b*128+nr-1 of the
-// padded order kp) over ncols columns: Yb points at row b*128 of the FP32 Y
-// (leading dimension ldy, a multiple of 4 with 16-byte aligned columns),
-// Ybf_b at the same element of its BF16 copy; inv16 holds the two-term split
-// of all block inverses (2 x kp rows of 128 BF16: hi rows first).
-int launch_apply_inverse_tc(const __nv_bfloat16 *inv16, int64_t kp, int64_t b, float *Yb, int64_t ldy,
-                            __nv_bfloat16 *Ybf_b, int nr, int64_t ncols, cudaStream_t s, int *status)
-{
-    if (nr <= 0 || ncols <= 0) return 0;
-    if (nr > TB || (nr % 4 && nr != TB) || kp % TB || ldy % 4 || (reinterpret_cast<uintptr_t>(Yb) & 15) ||
-        (reinterpret_cast<uintptr_t>(inv16) & 15) || 2 * kp > 0x7fffffffLL)
-        return GB_STATUS_CUDA_ERROR;
-    CUtensorMap tm;
-    {
-        uint64_t dims[2] = {uint64_t(TB), uint64_t(2 * kp)};
-        uint64_t strides[1] = {uint64_t(TB) * 2};
-        uint32_t box[2] = {64, TB};
-        GB_TRY(encode_tmap(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, inv16, dims, strides, box));
-    }
-    GB_TRY(apply_tc_prepare());
-    int *st = status ? status : device_status_word();
-    if (!st) return GB_STATUS_CUDA_ERROR;
-    const int64_t grid = (ncols + TB - 1) / TB;
-    LaunchScope ls(KK_DIAG, s, 3.0 * 2.0 * TB * TB * double(ncols), 4.0 * TB * TB * 2 + 10.0 * double(nr) * ncols);
-    return check(launch_pdl(apply_inverse_tc_kernel, dim3((unsigned)grid), dim3(NTH), SMEM_BYTES, s, tm,
-                            int(b * TB), int(kp + b * TB), Yb, ldy, Ybf_b, nr, ncols, st));
-}
-
-}  // namespace gb
-
-namespace gb {
-
 // Left-looking leaf step of the low-precision solve on block b0 (a multiple
 // of 128) of a leaf starting at s0 <= b0: Y(b0:b0+128, :) -= Mv(b0.., s0:b0)
 // X(s0:b0, :), then X_b = L_b^-1 Y_b (FP32 and BF16 copies), over all np
 // columns.  Abf: BF16 Mv, row-major, leading dimension kp; Y / Ybf: the FP32
-// right-hand side and its BF16 copy (column-major, kp); inv16 as above.
+// right-hand side and its BF16 copy (column-major, kp); inv16: the inverses'
+// high terms in rows b*128.., their low terms in rows kp + b*128.. (128 wide).
 int launch_leaf_step_tc(const __nv_bfloat16 *Abf, const __nv_bfloat16 *inv16, int64_t kp, int64_t np, int64_t b0,
                         int64_t s0, float *Y, __nv_bfloat16 *Ybf, cudaStream_t s, int *status)
 {

@@ -22,6 +22,7 @@
 // end.  Sizes are padded to multiples of 128 (identity on the padded
 // diagonal, zero right-hand sides), so every tile is aligned for TMA.
 #include <cmath>
+#include <algorithm>
 #include <cstdio>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -48,8 +49,6 @@ int launch_invert_blocks(const float *band, float *inv, __nv_bfloat16 *inv16, in
 int apply_tc_prepare();
 int launch_leaf_step_tc(const __nv_bfloat16 *Abf, const __nv_bfloat16 *inv16, int64_t kp, int64_t np, int64_t b0,
                         int64_t s0, float *Y, __nv_bfloat16 *Ybf, cudaStream_t s, int *status);
-int launch_apply_inverse_tc(const __nv_bfloat16 *inv16, int64_t kp, int64_t b, float *Yb, int64_t ldy,
-                            __nv_bfloat16 *Ybf_b, int nr, int64_t ncols, cudaStream_t s, int *status);
 namespace {
 
 constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
@@ -725,73 +724,118 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec)
     return L;
 }
 
-int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
-               int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
-               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph, cudaEvent_t b_ready)
+// Pointers into a work space laid out by mixed_layout.
+struct MixedBufs {
+    __nv_bfloat16 *Abf, *As, *binv16, *Ybf, *Zs;
+    float *band, *binv, *Y, *xmax;
+    double *R, *X, *norms, *dg;
+    long long *Tg;
+    int *e_row, *f_col;
+    uint8_t *A8, *Y8;
+    unsigned *bmax;
+    float *bscale, *sY;
+};
+
+static MixedBufs mixed_bufs(const MixedLayout &L, char *ws, bool fp8)
 {
-    const int64_t k = side == GB_LEFT ? m : n;
-    const int64_t ncols = side == GB_LEFT ? n : m;
+    MixedBufs b;
+    b.Abf = reinterpret_cast<__nv_bfloat16 *>(ws + L.o_abf);
+    b.As = reinterpret_cast<__nv_bfloat16 *>(ws + L.o_as);
+    b.binv16 = fp8 ? nullptr : reinterpret_cast<__nv_bfloat16 *>(ws + L.o_binv16);
+    b.Ybf = reinterpret_cast<__nv_bfloat16 *>(ws + L.o_ybf);
+    b.Zs = reinterpret_cast<__nv_bfloat16 *>(ws + L.o_zs);
+    b.band = reinterpret_cast<float *>(ws + L.o_band);
+    b.binv = reinterpret_cast<float *>(ws + L.o_binv);
+    b.Y = reinterpret_cast<float *>(ws + L.o_y);
+    b.xmax = reinterpret_cast<float *>(ws + L.o_xm);
+    b.R = reinterpret_cast<double *>(ws + L.o_r);
+    b.X = reinterpret_cast<double *>(ws + L.o_x);
+    b.norms = reinterpret_cast<double *>(ws + L.o_norm);
+    b.dg = reinterpret_cast<double *>(ws + L.o_dg);
+    b.Tg = reinterpret_cast<long long *>(ws + L.o_t);
+    b.e_row = reinterpret_cast<int *>(ws + L.o_e);
+    b.f_col = reinterpret_cast<int *>(ws + L.o_f);
+    b.A8 = fp8 ? reinterpret_cast<uint8_t *>(ws + L.o_a8) : nullptr;
+    b.Y8 = fp8 ? reinterpret_cast<uint8_t *>(ws + L.o_y8) : nullptr;
+    b.bmax = fp8 ? reinterpret_cast<unsigned *>(ws + L.o_bmax) : nullptr;
+    b.bscale = fp8 ? reinterpret_cast<float *>(ws + L.o_bscale) : nullptr;
+    b.sY = fp8 ? reinterpret_cast<float *>(ws + L.o_sy) : nullptr;
+    return b;
+}
+
+// forward = the canonical view is a forward (lower) substitution
+static bool mixed_forward(int side, int uplo, int trans)
+{
     const bool mt = side == GB_LEFT ? (trans == GB_TRANS) : (trans == GB_NOTRANS);
-    const bool forward = (uplo == GB_LOWER) != mt;
-    const MixedLayout L = mixed_layout(side, m, n, prec);
+    return (uplo == GB_LOWER) != mt;
+}
+
+int mixed_prep_a(int side, int uplo, int trans, int diag, int64_t k, const double *A, int64_t lda, int prec,
+                 const MixedLayout &L, char *ws, cudaStream_t s)
+{
+    const bool mt = side == GB_LEFT ? (trans == GB_TRANS) : (trans == GB_NOTRANS);
+    const bool forward = mixed_forward(side, uplo, trans);
+    const bool fp8 = prec == GB_PREC_FP8;
+    const int64_t kp = L.kp;
+    const MixedBufs bf = mixed_bufs(L, ws, fp8);
+    View v{A, lda, mt, !forward, diag == GB_UNIT, k};
+    GB_CUDA(cudaMemsetAsync(bf.e_row, 0x80, size_t(kp) * 4, s));  // very negative
+    dim3 tgrid((unsigned)(kp / 64), (unsigned)(kp / 64));
+    {
+        LaunchScope ls(KK_CONVERT, s, 0, 8.0 * double(k) * double(k) / 2);
+        if (fp8) GB_CUDA(cudaMemsetAsync(bf.bmax, 0, size_t(kp / 128) * (kp / 128) * 4, s));
+        rowexp_kernel<<<tgrid, 256, 0, s>>>(v, kp, bf.e_row, bf.bmax);
+        GB_CUDA(cudaGetLastError());
+    }
+    {
+        LaunchScope ls(KK_CONVERT, s, 0, (8.0 + 2.0 * (1 + kSlices)) * double(kp) * double(kp) / 2);
+        if (fp8) {
+            const int64_t nbb = (kp / 128) * (kp / 128);
+            block_scales_kernel<<<(unsigned)((nbb + 255) / 256), 256, 0, s>>>(bf.bmax, bf.bscale, nbb);
+            GB_CUDA(cudaGetLastError());
+        }
+        prepA_kernel<<<tgrid, 256, 0, s>>>(v, kp, bf.e_row, bf.Abf, bf.As, bf.band, bf.dg, bf.A8, bf.bscale);
+        GB_CUDA(cudaGetLastError());
+    }
+    return launch_invert_blocks(bf.band, bf.binv, bf.binv16, kp / kBand, s);
+}
+
+int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, double alpha, const double *B,
+                  int64_t ldb, double *Bout, int64_t ldbo, double tol, int prec, int max_iter, int *iters_out,
+                  double *est_err_out, cudaStream_t s, char *ws, const MixedLayout &L, int *status_word,
+                  bool use_graph, cudaEvent_t b_ready, bool merge_hist)
+{
+    const bool forward = mixed_forward(side, uplo, trans);
     const int64_t kp = L.kp, np = L.np;
     const bool fp8 = prec == GB_PREC_FP8;
-    uint8_t *A8 = fp8 ? reinterpret_cast<uint8_t *>(ws + L.o_a8) : nullptr;
-    unsigned *bmax = fp8 ? reinterpret_cast<unsigned *>(ws + L.o_bmax) : nullptr;
-    float *bscale = fp8 ? reinterpret_cast<float *>(ws + L.o_bscale) : nullptr;
-    uint8_t *Y8 = fp8 ? reinterpret_cast<uint8_t *>(ws + L.o_y8) : nullptr;
-    float *sY = fp8 ? reinterpret_cast<float *>(ws + L.o_sy) : nullptr;
     const size_t kn = size_t(kp) * size_t(np);
-
-    View v{A, lda, mt, !forward, diag == GB_UNIT, k};
-    tl_nhist = 0;
-    const size_t o_abf = L.o_abf, o_as = L.o_as, o_band = L.o_band, o_binv = L.o_binv, o_r = L.o_r, o_x = L.o_x;
-    const size_t o_y = L.o_y, o_ybf = L.o_ybf, o_zs = L.o_zs, o_e = L.o_e, o_f = L.o_f, o_norm = L.o_norm;
-    const size_t o_dg = L.o_dg, o_xm = L.o_xm;
-    auto *Abf = reinterpret_cast<__nv_bfloat16 *>(ws + o_abf);
-    auto *As = reinterpret_cast<__nv_bfloat16 *>(ws + o_as);
-    auto *band = reinterpret_cast<float *>(ws + o_band);
-    auto *binv = reinterpret_cast<float *>(ws + o_binv);
-    auto *R = reinterpret_cast<double *>(ws + o_r);
-    auto *Tg = reinterpret_cast<long long *>(ws + L.o_t);
-    auto *X = reinterpret_cast<double *>(ws + o_x);
-    auto *Y = reinterpret_cast<float *>(ws + o_y);
-    auto *Ybf = reinterpret_cast<__nv_bfloat16 *>(ws + o_ybf);
-    auto *Zs = reinterpret_cast<__nv_bfloat16 *>(ws + o_zs);
-    auto *e_row = reinterpret_cast<int *>(ws + o_e);
-    auto *f_col = reinterpret_cast<int *>(ws + o_f);
-    auto *norms = reinterpret_cast<double *>(ws + o_norm);
-    auto *dg = reinterpret_cast<double *>(ws + o_dg);
-    auto *xmax = reinterpret_cast<float *>(ws + o_xm);
+    const MixedBufs bf = mixed_bufs(L, ws, fp8);
+    auto *Abf = bf.Abf;
+    auto *As = bf.As;
+    auto *binv = bf.binv;
+    auto *R = bf.R;
+    auto *Tg = bf.Tg;
+    auto *X = bf.X;
+    auto *Y = bf.Y;
+    auto *Ybf = bf.Ybf;
+    auto *Zs = bf.Zs;
+    auto *e_row = bf.e_row;
+    auto *f_col = bf.f_col;
+    auto *norms = bf.norms;
+    auto *dg = bf.dg;
+    auto *xmax = bf.xmax;
+    // history of this solve: from scratch, or merged (step-wise maximum)
+    // into that of the previous column block of the same problem
+    const int hist0 = merge_hist ? tl_nhist : 0;
+    int hist = 0;
+    if (!merge_hist) tl_nhist = 0;
 
     int st = 0;
     double h_norm[4] = {0, 0, 0, 0};
     int iters = 0;
     double est = 0;
     do {
-        // ---- conversions (once per solve) ----
-        if ((st = check(cudaMemsetAsync(e_row, 0x80, size_t(kp) * 4, s)))) break;  // very negative
-        dim3 tgrid((unsigned)(kp / 64), (unsigned)(kp / 64));
-        {
-            LaunchScope ls(KK_CONVERT, s, 0, 8.0 * double(k) * double(k) / 2);
-            if (fp8 && (st = check(cudaMemsetAsync(bmax, 0, size_t(kp / 128) * (kp / 128) * 4, s)))) break;
-            rowexp_kernel<<<tgrid, 256, 0, s>>>(v, kp, e_row, bmax);
-            if ((st = check(cudaGetLastError()))) break;
-        }
-        {
-            LaunchScope ls(KK_CONVERT, s, 0, (8.0 + 2.0 * (1 + kSlices)) * double(kp) * double(kp) / 2);
-            if (fp8) {
-                const int64_t nbb = (kp / 128) * (kp / 128);
-                block_scales_kernel<<<(unsigned)((nbb + 255) / 256), 256, 0, s>>>(bmax, bscale, nbb);
-                if ((st = check(cudaGetLastError()))) break;
-            }
-            prepA_kernel<<<tgrid, 256, 0, s>>>(v, kp, e_row, Abf, As, band, dg, A8, bscale);
-            if ((st = check(cudaGetLastError()))) break;
-        }
-        auto *binv16 = fp8 ? nullptr : reinterpret_cast<__nv_bfloat16 *>(ws + L.o_binv16);
-        if ((st = launch_invert_blocks(band, binv, binv16, kp / kBand, s))) break;
-        // everything above needs only A: the right-hand sides may still be
-        // arriving on another stream
+        // the right-hand sides may still be arriving on another stream
         if (b_ready && (st = check(cudaStreamWaitEvent(s, b_ready, 0)))) break;
         {
             LaunchScope ls(KK_CONVERT, s, 0, 16.0 * double(kp) * double(np));
@@ -800,12 +844,12 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
             if ((st = check(cudaGetLastError()))) break;
         }
         LowExec le{Y, Ybf, Abf, binv, kp, np, s, status_word};
-        le.binv16 = binv16;
+        le.binv16 = bf.binv16;
         le.fp8 = fp8;
-        le.A8 = A8;
-        le.sA = bscale;
-        le.Y8 = Y8;
-        le.sY = sY;
+        le.A8 = bf.A8;
+        le.sA = bf.bscale;
+        le.Y8 = bf.Y8;
+        le.sY = bf.sY;
         LowGraph *lg = nullptr;
         if (use_graph && (st = low_graph(le, ws, &lg))) break;
         const int64_t nel = int64_t(kn);
@@ -853,10 +897,16 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
             const double nd = std::sqrt(h_norm[0]);
             if (t == 0) nx = std::sqrt(h_norm[1]);
             const double rho = nx > 0 ? nd / nx : 0.0;
-            if (t > 0 && tl_nhist < 64) {
-                tl_rho[tl_nhist] = rho;
-                tl_levels[tl_nhist] = Lmax;
-                tl_nhist++;
+            if (t > 0 && hist < 64) {
+                if (hist < hist0) {
+                    tl_rho[hist] = std::max(tl_rho[hist], rho);
+                    tl_levels[hist] = std::max(tl_levels[hist], Lmax);
+                } else {
+                    tl_rho[hist] = rho;
+                    tl_levels[hist] = Lmax;
+                    tl_nhist = hist + 1;
+                }
+                hist++;
             }
             if (t > 0) {
                 iters = t;
@@ -883,7 +933,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
         {
             LaunchScope ls(KK_CONVERT, s, 0, 16.0 * double(k) * double(ncols));
             writeback_kernel<<<dim3((unsigned)(np / 64), (unsigned)(kp / 64)), 256, 0, s>>>(
-                B, ldb, side == GB_LEFT, !forward, k, ncols, X, kp, np, Zs, f_col, nz);
+                Bout, ldbo, side == GB_LEFT, !forward, k, ncols, X, kp, np, Zs, f_col, nz);
             if ((st = check(cudaGetLastError()))) break;
         }
     } while (0);
@@ -897,6 +947,21 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
     return (est <= tol) ? 0 : GB_STATUS_NOT_CONVERGED;
 }
 
+
+int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
+               int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
+               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph, cudaEvent_t b_ready)
+{
+    const int64_t k = side == GB_LEFT ? m : n;
+    const int64_t ncols = side == GB_LEFT ? n : m;
+    const MixedLayout L = mixed_layout(side, m, n, prec);
+    tl_nhist = 0;
+    if (iters_out) *iters_out = 0;
+    if (est_err_out) *est_err_out = 0;
+    GB_TRY(mixed_prep_a(side, uplo, trans, diag, k, A, lda, prec, L, ws, s));
+    return mixed_solve_b(side, uplo, trans, k, ncols, alpha, B, ldb, B, ldb, tol, prec, max_iter, iters_out,
+                         est_err_out, s, ws, L, status_word, use_graph, b_ready, false);
+}
 
 cudaMemPool_t mixed_pool() { return library_pool(); }
 

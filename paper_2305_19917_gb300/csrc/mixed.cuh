@@ -27,6 +27,22 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
                int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
                double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph,
                cudaEvent_t b_ready);
+// The two halves of mixed_core, for callers that solve several column blocks
+// of one problem against one preparation of A (the work space laid out for
+// the widest block, L.np >= every block's ncols):
+//  - mixed_prep_a: the work that needs only A (row exponents, digit slices,
+//    BF16 copy, diagonal-block inverses);
+//  - mixed_solve_b: the refinement solve of one block of ncols right-hand
+//    sides read from B (ldb) and written to Bout (ldbo; may be B), given in
+//    the user's orientation (columns of B for side = left, rows for right).
+//    merge_hist folds this block's refinement history into the previous
+//    block's (step-wise maximum) instead of starting a new one.
+int mixed_prep_a(int side, int uplo, int trans, int diag, int64_t k, const double *A, int64_t lda, int prec,
+                 const MixedLayout &L, char *ws, cudaStream_t s);
+int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, double alpha, const double *B,
+                  int64_t ldb, double *Bout, int64_t ldbo, double tol, int prec, int max_iter, int *iters_out,
+                  double *est_err_out, cudaStream_t s, char *ws, const MixedLayout &L, int *status_word,
+                  bool use_graph, cudaEvent_t b_ready, bool merge_hist);
 // The library's stream-ordered memory pool for work space (current device).
 cudaMemPool_t mixed_pool();
 

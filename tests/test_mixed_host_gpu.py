@@ -52,3 +52,49 @@ def test_host_entry_rejects_device_tensors():
     A = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
     with pytest.raises(ValueError):
         api.trsm_mixed_host(0, 0, 0, 0, 1.0, A, A)
+
+
+@pytest.mark.parametrize("blocks", [2, 3])
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("side,uplo,trans,diag,m,n,alpha", [
+    (0, 0, 0, 0, 300, 330, 1.5), (0, 1, 1, 1, 200, 260, -0.5), (1, 0, 1, 0, 390, 180, 2.0),
+    (1, 1, 0, 0, 257, 140, 1.0)])
+def test_pipelined_column_blocks_match_oracle(monkeypatch, blocks, pinned, side, uplo, trans, diag, m, n, alpha):
+    """The host solve in 2 or 3 column blocks (ragged last block; columns of B
+    for side = left, rows for right) gives the oracle's solution in every
+    block, and the per-solve report covers all of them."""
+    from paper_2305_19917_gb300 import api
+    monkeypatch.setenv("GB_MIXED_HOST_BLOCKS", str(blocks))
+    A, B = inputs.make_problem(side, uplo, trans, diag, m, n, seed=11, poison=True)
+    Xo = oracle.dtrsm(side, uplo, trans, diag, alpha, A, B)
+    Ah, Bh = _host(A, pinned), _host(B, pinned)
+    st, it, est = api.trsm_mixed_host(side, uplo, trans, diag, alpha, Ah, Bh)
+    X = Bh.numpy()
+    assert st == 0 and it >= 1 and 0 < est <= 1e-11
+    assert np.isfinite(X).all()
+    # every right-hand side (column of X for left, row for right) on its own
+    Xc, Oc = (X, Xo) if side == 0 else (X.T, Xo.T)
+    for j in range(Xc.shape[1]):
+        assert np.linalg.norm(Xc[:, j] - Oc[:, j]) <= TOL * np.linalg.norm(Oc[:, j]), j
+    hist = api.gb_mixed_history()  # merged over the blocks: the longest refinement
+    assert len(hist) == it and all(r > 0 for r, _ in hist)
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_pipelined_failure_in_a_later_block_leaves_b_unchanged(monkeypatch, side):
+    """A right-hand side beyond the FP32 range in the second block returns
+    GB_STATUS_RANGE after the first block's solution already went back to
+    the host: the library restores it, and B is left exactly as it was."""
+    from paper_2305_19917_gb300 import api
+    monkeypatch.setenv("GB_MIXED_HOST_BLOCKS", "2")
+    m, n = (200, 300) if side == 0 else (300, 200)
+    A, B = inputs.make_problem(side, 0, 0, 0, m, n, seed=12)
+    if side == 0:
+        B[:, 280] *= 1e300   # block 2 = columns 256..299
+    else:
+        B[280, :] *= 1e300   # block 2 = rows 256..299
+    Bh = _host(B, True)
+    B0 = Bh.numpy().copy()
+    st, it, est = api.trsm_mixed_host(side, 0, 0, 0, 1.0, _host(A, True), Bh)
+    assert st == api.STATUS_RANGE
+    assert np.array_equal(Bh.numpy(), B0)
