@@ -140,9 +140,12 @@ enum { GB_PREC_BF16 = 0, GB_PREC_FP8 = 1 };
  * Returns 0 when converged, GB_STATUS_NOT_CONVERGED (X = last iterate) when
  * max_iter was reached first.  The residual's exact digit sums bound the
  * attainable accuracy near 2^-48 |op(A)||X| (a tol much below 1e-13 is not
- * reached), and the low-precision solve needs alpha*B and X within the FP32
- * range (about 3.4e38): values beyond it (or non-finite ones) return
- * GB_STATUS_RANGE with B unchanged.
+ * reached).  Each right-hand side is scaled by an exact power of two (its
+ * largest |alpha*B| entry brought near 1) for the low-precision solve and
+ * scaled back on output, so the scale of B does not matter; but the scaled
+ * solution must stay within the FP32 range of that solve (about 3.4e38 times
+ * the column's largest |alpha*B|): beyond it, or with non-finite data, the
+ * call returns GB_STATUS_RANGE with B unchanged.
  * Synchronous: returns after the solve is complete.  Work space (about
  * 14 k^2 + 42 k n bytes, k and n rounded up to multiples of 128) comes from a
  * library-owned stream-ordered pool.
@@ -160,7 +163,7 @@ int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
  * library image (held on every GPU that loads the library until the process
  * exits).  That bounds the problem: the padded sizes kp = 128*ceil(k/128),
  * np = 128*ceil(ncols/128) (k = order of A, ncols = right-hand sides) must
- * satisfy roughly 14 kp^2 + 42 kp np + 1550 kp + 16 np + 4 KB <= 16 MiB
+ * satisfy roughly 14 kp^2 + 42 kp np + 1550 kp + 20 np + 4 KB <= 16 MiB
  * (e.g. k = ncols = 512); larger problems return GB_STATUS_SCRATCH_TOO_SMALL
  * without touching the GPU.  The first call on a device performs a one-time
  * set-up (it looks up the array's device address), so make it before any

@@ -61,6 +61,12 @@ constexpr int kZSlots = 3;
 constexpr int kBand = 128;     // FP32 band of diagonal 128-blocks (column-major per block)
 constexpr int kLeaf = 1024;    // leaf order of the BF16 low-precision solve (8 fused leaf steps)
 
+// Library fallback of the integer-built conversions below, for results
+// outside the normal double range.  Kept out of line: inlined, the compiler
+// may evaluate it on every element (its int -> double conversion and scaling
+// run on the FP64 pipe) and select the result afterwards.
+__device__ __noinline__ double ldexp_i64_slow(long long t, int e) { return ldexp(static_cast<double>(t), e); }
+
 // z * 2^e as a double for |z| < 2^31 (exact: no rounding), built with 32-bit
 // integer operations (an int -> double conversion runs on the FP64 pipe,
 // which retires two operations per clock and SM); results outside the
@@ -72,11 +78,65 @@ __device__ __forceinline__ double scaled_i32_to_f64(int z, int e)
     const unsigned u = z < 0 ? 0u - unsigned(z) : unsigned(z);
     const int lz = __clz(int(u));
     const int ex = 31 - lz + e;
-    if (ex < -1022 || ex > 1023) return ldexp(double(z), e);
+    if (ex < -1022 || ex > 1023) return ldexp_i64_slow(z, e);
     const unsigned m = (lz == 31) ? 0u : (u << (lz + 1));  // fraction bits below the leading one
     const unsigned hi = sign | (unsigned(ex + 1023) << 20) | (m >> 12);
     const unsigned lo = m << 20;
     return __hiloint2double(int(hi), int(lo));
+}
+
+// T * 2^e rounded to the nearest double (ties to even), i.e. the value of
+// ldexp((double)T, e), for |T| < 2^63, built with integer operations (the
+// FP64 pipe retires two operations per clock and SM); results outside the
+// normal exponent range take the library path.
+__device__ __forceinline__ double scaled_i64_to_f64(long long T, int e)
+{
+    if (T == 0) return 0.0;
+    const unsigned long long sign = T < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long u = T < 0 ? 0ull - static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T);
+    const int lz = __clzll(static_cast<long long>(u));
+    int msb = 63 - lz;
+    const unsigned long long m = u << lz;  // leading one at bit 63
+    unsigned long long keep = m >> 11;     // 53 significant bits
+    const unsigned long long rem = m & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (keep & 1ull))) keep++;
+    if (keep >> 53) {  // rounded up to the next power of two
+        keep >>= 1;
+        msb++;
+    }
+    const int ex = msb + e;
+    if (ex < -1022 || ex > 1023) return ldexp_i64_slow(T, e);
+    return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(ex + 1023) << 52) |
+                                                       (keep & ((1ull << 52) - 1))));
+}
+
+// x rounded to the nearest float (ties to even), as __double2float_rn(x),
+// from the bit pattern with integer operations only (no FP64 instruction),
+// subnormal, overflowing and non-finite cases included.
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
+    const int E = int((b >> 52) & 0x7FF);
+    const unsigned long long mant = b & ((1ull << 52) - 1);
+    if (E >= 1023 - 126) {  // a normal float or beyond
+        if (E == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (mant ? 0x00400000u : 0u));
+        if (E > 1023 + 127) return __uint_as_float(sign | 0x7F800000u);
+        unsigned int keep = static_cast<unsigned int>(mant >> 29);
+        const unsigned long long rem = mant & ((1ull << 29) - 1);
+        if (rem > (1ull << 28) || (rem == (1ull << 28) && (keep & 1u))) keep++;
+        // a carry out of the mantissa moves into the exponent field, as it must
+        return __uint_as_float((sign | (static_cast<unsigned int>(E - 1023 + 127) << 23)) + keep);
+    }
+    // a subnormal float: round(M 2^(E - 1075 + 149)) units of 2^-149, M the
+    // 53-bit significand (zero below a quarter unit; double subnormals too)
+    const int r = 926 - E;
+    if (E == 0 || r >= 55) return __uint_as_float(sign);
+    const unsigned long long M = mant | (1ull << 52);
+    unsigned long long q = M >> r;
+    const unsigned long long rem = M & ((1ull << r) - 1), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (q & 1ull))) q++;
+    return __uint_as_float(sign | static_cast<unsigned int>(q));
 }
 
 // Canonical forward view of the user problem (device-side description).
@@ -103,16 +163,33 @@ __device__ __forceinline__ double mvp(const View &v, int64_t i, int64_t c)
 // Which index of Mv' runs along A's contiguous dimension: true = i.
 __device__ __forceinline__ bool contig_i(const View &v) { return !v.mt; }
 
+// The 16 entries of the 64 x 64 tile (i0.., c0..) of Mv' that thread tid of
+// 256 reads along A's contiguous dimension: entry u is (li, lc) with the
+// fast index tid & 63 and the slow one (tid >> 6) + 4u (li fast when
+// contig_i).  All 16 loads are issued before any is used.
+__device__ __forceinline__ void load_vals(const View &v, int64_t i0, int64_t c0, double (&val)[16])
+{
+    const int tid = threadIdx.x;
+    const bool ci = contig_i(v);
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+        const int fast = tid & 63, slow = (tid >> 6) + 4 * u;
+        val[u] = mvp(v, i0 + (ci ? fast : slow), c0 + (ci ? slow : fast));
+    }
+}
+
 // Load the 64 x 64 tile (i0.., c0..) of Mv' into shared memory t[64][65],
 // reading A along its contiguous dimension.
 __device__ void load_tile(const View &v, int64_t i0, int64_t c0, double (*t)[65])
 {
     const int tid = threadIdx.x;  // 256 threads
-    for (int idx = tid; idx < 64 * 64; idx += 256) {
-        int fast = idx & 63, slow = idx >> 6;
-        int li = contig_i(v) ? fast : slow;
-        int lc = contig_i(v) ? slow : fast;
-        t[li][lc] = mvp(v, i0 + li, c0 + lc);
+    const bool ci = contig_i(v);
+    double val[16];
+    load_vals(v, i0, c0, val);
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+        const int fast = tid & 63, slow = (tid >> 6) + 4 * u;
+        t[ci ? fast : slow][ci ? slow : fast] = val[u];
     }
 }
 
@@ -136,22 +213,36 @@ __device__ __forceinline__ int bexp(double a)
 // block scales.
 __global__ void __launch_bounds__(256) rowexp_kernel(View v, int64_t kp, int *e_row, unsigned *bmax)
 {
-    __shared__ double t[64][65];
+    __shared__ int rmax[64];
     __shared__ float red[8];
     const int64_t i0 = int64_t(blockIdx.y) * 64, c0 = int64_t(blockIdx.x) * 64;
     if (c0 > i0 + 63) return;
-    load_tile(v, i0, c0, t);
-    __syncthreads();
     const int tid = threadIdx.x;
-    if (tid < 64) {
+    if (tid < 64) rmax[tid] = 0;
+    double val[16];
+    load_vals(v, i0, c0, val);
+    __syncthreads();
+    const int fast = tid & 63;
+    if (contig_i(v)) {  // the thread's 16 entries share row fast
         int mx = 0;
-        for (int c = 0; c < 64; c++)
-            if (c0 + c != i0 + tid) mx = max(mx, bexp(t[tid][c]));
-        if (mx > 0) atomicMax(&e_row[i0 + tid], mx - 1023 + 2);
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+            if (c0 + (tid >> 6) + 4 * u != i0 + fast) mx = max(mx, bexp(val[u]));
+        if (mx > 0) atomicMax(&rmax[fast], mx);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            const int li = (tid >> 6) + 4 * u;
+            const int b = bexp(val[u]);
+            if (c0 + fast != i0 + li && b > 0) atomicMax(&rmax[li], b);
+        }
     }
+    __syncthreads();
+    if (tid < 64 && rmax[tid] > 0) atomicMax(&e_row[i0 + tid], rmax[tid] - 1023 + 2);
     if (bmax && (c0 >> 7) < (i0 >> 7)) {
         float m = 0.f;
-        for (int idx = tid; idx < 64 * 64; idx += 256) m = fmaxf(m, fabsf(float(t[idx >> 6][idx & 63])));
+#pragma unroll
+        for (int u = 0; u < 16; u++) m = fmaxf(m, fabsf(float(val[u])));
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((tid & 31) == 0) red[tid >> 5] = m;
         __syncthreads();
@@ -238,7 +329,7 @@ prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bflo
         size_t off = size_t(i) * size_t(kp) + size_t(c);
         Abf[off] = d2bf16(a);
         if (A8 && (c >> 7) < (i >> 7))
-            A8[off] = __nv_cvt_float_to_fp8(float(a) / bscale[(i >> 7) * (kp >> 7) + (c >> 7)], __NV_SATFINITE,
+            A8[off] = __nv_cvt_float_to_fp8(f64_to_f32_rn(a) / bscale[(i >> 7) * (kp >> 7) + (c >> 7)], __NV_SATFINITE,
                                             __NV_E4M3);
         // balanced base-256 digits of N = round(a 2^(48-e)): N = sum_p q_p 256^(6-p),
         // q_p in [-128, 128]; least significant first
@@ -251,19 +342,111 @@ prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bflo
             N = (N - d) >> 8;
         }
         As[off] = __int2bfloat16_rn(int(N));  // top digit, |N| <= 128
-        if (c / kBand == i / kBand) band[size_t(c) * kBand + (i % kBand)] = float(a);
+        if (c / kBand == i / kBand) band[size_t(c) * kBand + (i % kBand)] = f64_to_f32_rn(a);
     }
 }
 
 // R = alpha * Bv' (forward view of the right-hand sides), zero padded.
 // Left: Bv(i,j) = B(i,j); Right: Bv(i,j) = B(j,i); reversal on i.
-__global__ void __launch_bounds__(256)
-prepB_kernel(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t ncols, double alpha,
-             double *R, float *Y, int64_t kp)
+// ---- right-hand sides: R = alpha B, scaled per column ------------------------
+// Every canonical column j of alpha B is scaled by the power of two 2^-c_j
+// that brings its largest entry near 1 (exact in FP64), so that the FP32 /
+// BF16 low-precision solve sees neither underflow nor overflow from the
+// scale of B; X is scaled back by 2^c_j when written.  With alpha = a 2^ea
+// (1 <= |a| < 2) and eb the exponent of max_i |B(i,j)| (clamped to
+// [-1000, 1000], so that both factors are normal doubles), c_j = ea + eb and
+// R(:,j) = B(:,j) * (a 2^-eb), one rounding, as alpha B(:,j) 2^-c_j.
+// Columns with a non-finite entry are left unscaled (the range check then
+// reports them).
+__device__ __forceinline__ int column_eb(int maxfield)
 {
-    __shared__ double t[64][65];
+    if (maxfield == 0x7FF) return 0;  // not finite
+    return max(-1000, min(1000, maxfield - 1023));  // zero / subnormal columns: 2^1000 up
+}
+__device__ __forceinline__ double pow2(int e)  // 2^e, -1022 <= e <= 1023
+{
+    return __longlong_as_double(static_cast<long long>(static_cast<unsigned long long>(e + 1023) << 52));
+}
+
+// Side = left (canonical columns = columns of B, rows reversed for a
+// backward problem), kp <= NT * VPT: one CTA of NT threads per column holds
+// the column in registers (VPT lane-contiguous values per thread), finds its
+// exponent, and writes R and Y = float(R) in one pass over B.
+template <int NT, int VPT>
+__global__ void __launch_bounds__(NT)
+prepB_cols_kernel(const double *B, int64_t ldb, bool rev, int64_t k, int64_t ncols, double am, int ea, double *R,
+                  float *Y, int *cs, int64_t kp)
+{
+    constexpr int NW = NT / 32;
+    __shared__ int red[NW];
+    const int64_t j = blockIdx.x;
+    double b[VPT];
+    int mf = 0;
+#pragma unroll
+    for (int q = 0; q < VPT; q++) {
+        const int64_t i = threadIdx.x + int64_t(q) * NT;
+        b[q] = (i < k && j < ncols) ? B[(rev ? k - 1 - i : i) + j * ldb] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < VPT; q++) mf = max(mf, bexp(b[q]));
+    mf = __reduce_max_sync(0xffffffffu, mf);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mf;
+    __syncthreads();
+    for (int w = 0; w < NW; w++) mf = max(mf, red[w]);
+    const int eb = column_eb(mf);
+    const double g = am * pow2(-eb);  // exact: a normal power of two times |a| in [1, 2)
+    if (threadIdx.x == 0) cs[j] = ea + eb;
+#pragma unroll
+    for (int q = 0; q < VPT; q++) {
+        const int64_t i = threadIdx.x + int64_t(q) * NT;
+        if (i < kp) {
+            const double v = b[q] * g;
+            R[i + j * kp] = v;
+            Y[i + j * kp] = f64_to_f32_rn(v);
+        }
+    }
+}
+
+// General case, pass 1: the largest exponent field of every canonical
+// column (atomic maximum into cmax, zero-initialised), 64 x 64 tiles read
+// along B's contiguous dimension.
+__global__ void __launch_bounds__(256)
+colexp_kernel(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t ncols, int *cmax)
+{
+    __shared__ int t[64];
     const int64_t i0 = int64_t(blockIdx.y) * 64, j0 = int64_t(blockIdx.x) * 64;
     const int tid = threadIdx.x;
+    if (tid < 64) t[tid] = 0;
+    __syncthreads();
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        int fast = idx & 63, slow = idx >> 6;
+        int li = left ? fast : slow, lj = left ? slow : fast;
+        int64_t i = i0 + li, j = j0 + lj;
+        if (i < k && j < ncols) {
+            int64_t r = rev ? k - 1 - i : i;
+            const int f = bexp(left ? B[r + j * ldb] : B[j + r * ldb]);
+            if (f > 0) atomicMax(&t[lj], f);
+        }
+    }
+    __syncthreads();
+    if (tid < 64 && t[tid] > 0) atomicMax(&cmax[j0 + tid], t[tid]);
+}
+
+// General case, pass 2: R = alpha B 2^-c (canonical layout, zero padding)
+// and Y = float(R) through a 64 x 64 shared-memory tile.
+__global__ void __launch_bounds__(256)
+prepB_kernel(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t ncols, double am, int ea,
+             double *R, float *Y, const int *cmax, int64_t kp)
+{
+    __shared__ double t[64][65];
+    __shared__ double gcol[64];
+    const int64_t i0 = int64_t(blockIdx.y) * 64, j0 = int64_t(blockIdx.x) * 64;
+    const int tid = threadIdx.x;
+    if (tid < 64) {
+        const int eb = column_eb(cmax[j0 + tid]);
+        gcol[tid] = am * pow2(-eb);
+    }
+    __syncthreads();
     for (int idx = tid; idx < 64 * 64; idx += 256) {
         int fast = idx & 63, slow = idx >> 6;
         int li = left ? fast : slow, lj = left ? slow : fast;
@@ -271,7 +454,7 @@ prepB_kernel(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64
         double val = 0.0;
         if (i < k && j < ncols) {
             int64_t r = rev ? k - 1 - i : i;
-            val = alpha * (left ? B[r + j * ldb] : B[j + r * ldb]);
+            val = (left ? B[r + j * ldb] : B[j + r * ldb]) * gcol[lj];
         }
         t[li][lj] = val;
     }
@@ -279,24 +462,141 @@ prepB_kernel(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64
     for (int idx = tid; idx < 64 * 64; idx += 256) {
         int li = idx & 63, lj = idx >> 6;
         R[(i0 + li) + (j0 + lj) * kp] = t[li][lj];
-        Y[(i0 + li) + (j0 + lj) * kp] = float(t[li][lj]);
+        Y[(i0 + li) + (j0 + lj) * kp] = f64_to_f32_rn(t[li][lj]);
     }
 }
 
-// X(i,j) from the digit slices of the first nz corrections: D_t = (256 z_1 +
-// z_2) 2^(f_t(j) - 16), summed as ((D_0 + D_1) + D_2) in FP64 like X += D_t.
-__device__ __forceinline__ double x_from_slots(const __nv_bfloat16 *Zs, const int *fz, int nz, int64_t kp,
-                                               int64_t np, int64_t i, int64_t j)
+// Pass 3: the column maxima become the exponents c_j, in place, once every
+// tile of pass 2 has read them.
+__global__ void colexp_finish_kernel(int *cs, int ea, int64_t np)
 {
-    const size_t kn = size_t(kp) * size_t(np), o = size_t(i) + size_t(j) * size_t(kp);
-    double x = 0.0;
-    for (int t = 0; t < nz; t++) {
-        const __nv_bfloat16 *z = Zs + size_t(t) * 2 * kn;
-        const int n = __bfloat162int_rn(z[o]) * 256 + __bfloat162int_rn(z[kn + o]);
-        const double d = scaled_i32_to_f64(n, fz[size_t(t) * np + j] - 16);
-        x = (t == 0) ? d : x + d;
+    const int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (j < np) cs[j] = ea + column_eb(cs[j]);
+}
+
+int launch_prepB(const double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t ncols, double am, int ea,
+                 double *R, float *Y, int *cs, int64_t kp, int64_t np, cudaStream_t s)
+{
+    const dim3 g((unsigned)np);
+    if (left && kp <= 2048)
+        prepB_cols_kernel<256, 8><<<g, 256, 0, s>>>(B, ldb, rev, k, ncols, am, ea, R, Y, cs, kp);
+    else if (left && kp <= 8192)
+        prepB_cols_kernel<512, 16><<<g, 512, 0, s>>>(B, ldb, rev, k, ncols, am, ea, R, Y, cs, kp);
+    else if (left && kp <= 16384)
+        prepB_cols_kernel<1024, 16><<<g, 1024, 0, s>>>(B, ldb, rev, k, ncols, am, ea, R, Y, cs, kp);
+    else {
+        GB_CUDA(cudaMemsetAsync(cs, 0, size_t(np) * 4, s));
+        const dim3 tg((unsigned)(np / 64), (unsigned)(kp / 64));
+        colexp_kernel<<<tg, 256, 0, s>>>(B, ldb, left, rev, k, ncols, cs);
+        GB_CUDA(cudaGetLastError());
+        prepB_kernel<<<tg, 256, 0, s>>>(B, ldb, left, rev, k, ncols, am, ea, R, Y, cs, kp);
+        GB_CUDA(cudaGetLastError());
+        colexp_finish_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(cs, ea, np);
     }
+    return check(cudaGetLastError());
+}
+
+// The kept corrections of column j: D_t = N_t 2^(f_t(j) - 16), N_t = 256 z_1 +
+// z_2 from the digit slices (|N_t| <= 2^15 + 2^7).  With f_min the smallest
+// f_t, X = (sum_t N_t 2^(f_t - f_min)) 2^(f_min - 16): when every shift is at
+// most 46 the sum is exact in an int64 and X is its one correct rounding (the
+// FP64 sum D_0 + D_1 + ... in order gives the same value whenever its first
+// additions are exact, the usual case); wider spreads add in FP64 in order.
+struct SlotCol {
+    int e;               // f_min - 16 + c_j (c_j: the column's scale exponent)
+    int sh[kZSlots];     // f_t - f_min
+    bool exact;          // the int64 sum applies
+    bool small;          // every shift <= 36: |sum| < 2^53, a double holds it unrounded
+};
+
+__device__ __forceinline__ SlotCol slot_col(const int *fz, int nz, int64_t np, int64_t j, int cj)
+{
+    SlotCol c;
+    int f[kZSlots];
+    int fmin = 0x7fffffff;
+#pragma unroll
+    for (int t = 0; t < kZSlots; t++) {
+        f[t] = t < nz ? fz[size_t(t) * np + j] : 0;
+        if (t < nz) fmin = min(fmin, f[t]);
+    }
+    c.e = fmin - 16 + cj;
+    c.exact = true;
+    c.small = true;
+#pragma unroll
+    for (int t = 0; t < kZSlots; t++) {
+        c.sh[t] = t < nz ? f[t] - fmin : 0;
+        c.exact = c.exact && c.sh[t] <= 46;  // 3 (2^15 + 2^7) 2^46 < 2^63
+        c.small = c.small && c.sh[t] <= 36;  // 3 (2^15 + 2^7) 2^36 < 2^53
+    }
+    return c;
+}
+
+// 256 z_1 + z_2 for integer-valued BF16 digits (|z| <= 128): exact in FP32,
+// read back as an integer through the 1.5 * 2^23 offset (|n| < 2^22).
+__device__ __forceinline__ int digit_pair(__nv_bfloat16 z1, __nv_bfloat16 z2)
+{
+    const float n = fmaf(__bfloat162float(z1), 256.0f, __bfloat162float(z2));
+    return __float_as_int(n + 12582912.0f) - 0x4B400000;
+}
+
+// S 2^e as a double for |S| < 2^53 (exact: no rounding), from the bit
+// pattern with integer operations; results outside the normal range take the
+// library path.
+__device__ __forceinline__ double scaled_i53_to_f64(long long S, int e)
+{
+    if (S == 0) return 0.0;
+    const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long u = S < 0 ? 0ull - static_cast<unsigned long long>(S) : static_cast<unsigned long long>(S);
+    const int lz = __clzll(static_cast<long long>(u));  // >= 11
+    const int ex = 63 - lz + e;
+    if (ex < -1022 || ex > 1023) return ldexp_i64_slow(S, e);
+    // leading one moved to bit 52 (the implicit bit, removed by the add
+    // of the exponent field minus one)
+    return __longlong_as_double(static_cast<long long>(
+        sign | ((u << (lz - 11)) + (static_cast<unsigned long long>(ex + 1022) << 52))));
+}
+
+// The FP64 sum of the corrections in order, for columns whose spread of
+// exponents is too wide for the int64 sum (out of line: rarely taken).
+__device__ __noinline__ double x_sum_f64(int n0, int n1, int n2, int nz, int e, int s0, int s1, int s2)
+{
+    double x = scaled_i32_to_f64(n0, e + s0);
+    if (nz > 1) x += scaled_i32_to_f64(n1, e + s1);
+    if (nz > 2) x += scaled_i32_to_f64(n2, e + s2);
     return x;
+}
+
+// X of one element (column parameters c) from its digits z[2t], z[2t+1] of
+// the first nz corrections.
+__device__ __forceinline__ double x_from_digits(const __nv_bfloat16 (&z)[2 * kZSlots], int nz, const SlotCol &c)
+{
+    static_assert(kZSlots == 3, "x_sum_f64 takes three corrections");
+    int N[kZSlots];
+#pragma unroll
+    for (int t = 0; t < kZSlots; t++) N[t] = t < nz ? digit_pair(z[2 * t], z[2 * t + 1]) : 0;
+    if (!c.exact) return x_sum_f64(N[0], N[1], N[2], nz, c.e, c.sh[0], c.sh[1], c.sh[2]);
+    long long S = 0;
+#pragma unroll
+    for (int t = 0; t < kZSlots; t++)
+        if (t < nz) S += static_cast<long long>(N[t]) << c.sh[t];
+    return c.small ? scaled_i53_to_f64(S, c.e) : scaled_i64_to_f64(S, c.e);
+}
+
+// The digits of element o (slot t at Zs + 2 t kn: z_1 plane, then z_2 plane).
+__device__ __forceinline__ void load_digits(__nv_bfloat16 (&z)[2 * kZSlots], const __nv_bfloat16 *Zs, int nz,
+                                            size_t kn, size_t o, bool in)
+{
+#pragma unroll
+    for (int u = 0; u < 2 * kZSlots; u++)
+        z[u] = (in && (u >> 1) < nz) ? Zs[size_t(u >> 1) * 2 * kn + size_t(u & 1) * kn + o] : __ushort_as_bfloat16(0);
+}
+
+__device__ __forceinline__ double x_from_slots(const __nv_bfloat16 *Zs, int nz, size_t kn, size_t o,
+                                               const SlotCol &c)
+{
+    __nv_bfloat16 z[2 * kZSlots];
+    load_digits(z, Zs, nz, kn, o, true);
+    return x_from_digits(z, nz, c);
 }
 
 // X = the sum of the kept corrections (when the refinement outgrows the slots).
@@ -304,21 +604,35 @@ __global__ void __launch_bounds__(256)
 fold_slots_kernel(double *X, const __nv_bfloat16 *Zs, const int *fz, int nz, int64_t kp, int64_t np)
 {
     const int64_t i = int64_t(blockIdx.y) * 256 + threadIdx.x, j = blockIdx.x;
-    if (i < kp) X[i + j * kp] = x_from_slots(Zs, fz, nz, kp, np, i, j);
+    const SlotCol c = slot_col(fz, nz, np, j, 0);  // X stays in the scaled units of the refinement
+    if (i < kp) X[i + j * kp] = x_from_slots(Zs, nz, size_t(kp) * size_t(np), size_t(i) + size_t(j) * size_t(kp), c);
 }
 
-// B(user) = X' mapped back (only the m x n user entries); X' is read from X
-// (nz == 0) or formed from the digit slices of the first nz corrections.
+// x 2^c for the column scale exponents c (|c| <= 2074): three factors, each
+// a normal power of two (only a product that leaves the normal range rounds).
+__device__ __forceinline__ double unscale(double x, int c)
+{
+    const int h = c / 3;
+    return x * pow2(h) * pow2(h) * pow2(c - 2 * h);
+}
+
+// B(user) = X' 2^c_j mapped back (only the m x n user entries); X' is read
+// from X (nz == 0) or formed from the digit slices of the first nz
+// corrections.  Side = right: B's contiguous index is the canonical column,
+// so 64 x 64 tiles pass through shared memory.
 __global__ void __launch_bounds__(256)
 writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t ncols, const double *X,
-                 int64_t kp, int64_t np, const __nv_bfloat16 *Zs, const int *fz, int nz)
+                 int64_t kp, int64_t np, const __nv_bfloat16 *Zs, const int *fz, int nz, const int *cs)
 {
     __shared__ double t[64][65];
     const int64_t i0 = int64_t(blockIdx.y) * 64, j0 = int64_t(blockIdx.x) * 64;
     const int tid = threadIdx.x;
+    const size_t kn = size_t(kp) * size_t(np);
     for (int idx = tid; idx < 64 * 64; idx += 256) {
         int li = idx & 63, lj = idx >> 6;
-        t[li][lj] = nz ? x_from_slots(Zs, fz, nz, kp, np, i0 + li, j0 + lj) : X[(i0 + li) + (j0 + lj) * kp];
+        const size_t o = size_t(i0 + li) + size_t(j0 + lj) * size_t(kp);
+        const int cj = cs[j0 + lj];
+        t[li][lj] = nz ? x_from_slots(Zs, nz, kn, o, slot_col(fz, nz, np, j0 + lj, cj)) : unscale(X[o], cj);
     }
     __syncthreads();
     for (int idx = tid; idx < 64 * 64; idx += 256) {
@@ -333,6 +647,39 @@ writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t
     }
 }
 
+// Side = left: B's columns are the canonical columns (rows reversed for a
+// backward problem; X' 2^c_j as above), so no transpose: one column per CTA row of the grid,
+// each warp 128 rows, 4 lane-contiguous rows per thread (coalesced digit
+// loads and B stores); all 24 digit loads of a thread are issued before any
+// arithmetic, to keep enough bytes in flight.
+__global__ void __launch_bounds__(256)
+writeback_left_kernel(double *B, int64_t ldb, bool rev, int64_t k, const double *X, int64_t kp, int64_t np,
+                      const __nv_bfloat16 *Zs, const int *fz, int nz, const int *cs)
+{
+    const int64_t j = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ib = (int64_t(blockIdx.y) * 8 + warp) * 128 + lane;
+    const size_t kn = size_t(kp) * size_t(np), o0 = size_t(ib) + size_t(j) * size_t(kp);
+    const int cj = cs[j];
+    double x[4];
+    if (nz == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) x[q] = (ib + 32 * q < kp) ? unscale(X[o0 + 32 * q], cj) : 0.0;
+    } else {
+        const SlotCol c = slot_col(fz, nz, np, j, cj);
+        __nv_bfloat16 z[4][2 * kZSlots];
+#pragma unroll
+        for (int q = 0; q < 4; q++) load_digits(z[q], Zs, nz, kn, o0 + 32 * q, ib + 32 * q < kp);
+#pragma unroll
+        for (int q = 0; q < 4; q++) x[q] = x_from_digits(z[q], nz, c);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int64_t i = ib + 32 * q;
+        if (i < k) B[(rev ? k - 1 - i : i) + j * ldb] = x[q];
+    }
+}
+
 // Per column j: f_j = E + 2 with 2^E <= max_k |Y(k,j)| < 2^(E+1); the
 // 16-bit value N = round(Y 2^(16-f_j)) (|N| <= 2^15, FP32 arithmetic, exact
 // scaling) split into balanced base-256 digits z_1, z_2 (N = 256 z_1 + z_2,
@@ -343,26 +690,46 @@ writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t
 // largest column ratio max|D~| / max|X| goes to norms[2] (as bits); a column
 // whose maximum is not a finite FP32 value (the low-precision solve left
 // the FP32 range, or the data are not finite) counts into norms[3].
-__global__ void __launch_bounds__(256)
+// One CTA of NT threads per column; with VPT > 0 (kp <= NT * VPT) the column
+// is read once into registers (VPT lane-contiguous values per thread),
+// otherwise (VPT = 0) it is read again for the second pass.
+template <int NT, int VPT>
+__global__ void __launch_bounds__(NT)
 slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bfloat16 *Zs, int *f_col,
                   double *X, float *xmax, double *norms, int first)
 {
+    constexpr int NW = NT / 32;
     const int64_t j = blockIdx.x;
     const float *y = Y + j * kp;
-    __shared__ float red[8];
-    __shared__ float redd[2][8];
+    __shared__ float red[NW];
+    __shared__ float redd[2][NW];
+    float v[VPT > 0 ? VPT : 1];
     float mx = 0.f;
     int bad = 0;  // a value that is not a finite FP32 number (fmaxf would skip a NaN)
-    for (int64_t i = threadIdx.x; i < kp; i += 256) {
-        const float a = fabsf(y[i]);
-        mx = fmaxf(mx, a);
-        bad |= !(a <= 3.4028235e38f);
+    if constexpr (VPT > 0) {
+#pragma unroll
+        for (int q = 0; q < VPT; q++) {
+            const int64_t i = threadIdx.x + int64_t(q) * NT;
+            v[q] = i < kp ? y[i] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < VPT; q++) {
+            const float a = fabsf(v[q]);
+            mx = fmaxf(mx, a);
+            bad |= !(a <= 3.4028235e38f);
+        }
+    } else {
+        for (int64_t i = threadIdx.x; i < kp; i += NT) {
+            const float a = fabsf(y[i]);
+            mx = fmaxf(mx, a);
+            bad |= !(a <= 3.4028235e38f);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     bad = __syncthreads_or(bad);
     mx = 0.f;
-    for (int w = 0; w < 8; w++) mx = fmaxf(mx, red[w]);
+    for (int w = 0; w < NW; w++) mx = fmaxf(mx, red[w]);
     const int be = int((__float_as_uint(mx) >> 23) & 0xFF);
     const int f = (be > 0) ? be - 127 + 2 : 0;
     if (threadIdx.x == 0) f_col[j] = f;
@@ -371,8 +738,8 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
     __nv_bfloat16 *z2 = Zs + np * kp + j * kp;
     double *x = X ? X + j * kp : nullptr;
     float sd = 0.f, sx = 0.f;
-    for (int64_t i = threadIdx.x; i < kp; i += 256) {
-        const int N = (be > 0) ? __float2int_rn(y[i] * up) : 0;
+    auto digits = [&](int64_t i, float yi) {
+        const int N = (be > 0) ? __float2int_rn(yi * up) : 0;
         const int q2 = ((N + 128) & 255) - 128;
         const int q1 = (N - q2) >> 8;
         z1[i] = __int2bfloat16_rn(q1);
@@ -384,6 +751,15 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
             else x[i] += dd;
         }
         sd = fmaf(d, d, sd);
+    };
+    if constexpr (VPT > 0) {
+#pragma unroll
+        for (int q = 0; q < VPT; q++) {
+            const int64_t i = threadIdx.x + int64_t(q) * NT;
+            if (i < kp) digits(i, v[q]);
+        }
+    } else {
+        for (int64_t i = threadIdx.x; i < kp; i += NT) digits(i, y[i]);
     }
     if (first) sx = sd;
     for (int o = 16; o > 0; o >>= 1) {
@@ -398,7 +774,7 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
     if (threadIdx.x == 0 && j < ncols && bad) atomicAdd(&norms[3], 1.0);
     if (threadIdx.x == 0 && j < ncols) {
         float a = 0.f, b = 0.f;
-        for (int w = 0; w < 8; w++) {
+        for (int w = 0; w < NW; w++) {
             a += redd[0][w];
             b += redd[1][w];
         }
@@ -414,73 +790,74 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
     }
 }
 
+void launch_slice_cols(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bfloat16 *Zs, int *f_col,
+                       double *X, float *xmax, double *norms, int first, cudaStream_t s)
+{
+    const dim3 g((unsigned)np);
+    if (kp <= 1024)
+        slice_cols_kernel<256, 4><<<g, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms, first);
+    else if (kp <= 2048)
+        slice_cols_kernel<256, 8><<<g, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms, first);
+    else if (kp <= 4096)
+        slice_cols_kernel<256, 16><<<g, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms, first);
+    else if (kp <= 8192)
+        slice_cols_kernel<256, 32><<<g, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms, first);
+    else if (kp <= 16384)
+        slice_cols_kernel<1024, 16><<<g, 1024, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms, first);
+    else if (kp <= 32768)
+        slice_cols_kernel<1024, 32><<<g, 1024, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms, first);
+    else
+        slice_cols_kernel<256, 0><<<g, 256, 0, s>>>(Y, kp, np, ncols, Zs, f_col, X, xmax, norms, first);
+}
+
 // ---- residual: FP64 application of the exact sums ------------------------------
-// T * 2^e rounded to the nearest double (ties to even), i.e. the value of
-// ldexp((double)T, e), for |T| < 2^63, built with integer operations (the
-// FP64 pipe retires two operations per clock and SM); results outside the
-// normal exponent range take the library path.
-__device__ __forceinline__ double scaled_i64_to_f64(long long T, int e)
-{
-    if (T == 0) return 0.0;
-    const unsigned long long sign = T < 0 ? (1ull << 63) : 0ull;
-    const unsigned long long u = T < 0 ? 0ull - static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T);
-    const int lz = __clzll(static_cast<long long>(u));
-    int msb = 63 - lz;
-    const unsigned long long m = u << lz;  // leading one at bit 63
-    unsigned long long keep = m >> 11;     // 53 significant bits
-    const unsigned long long rem = m & 0x7FFull;
-    if (rem > 0x400ull || (rem == 0x400ull && (keep & 1ull))) keep++;
-    if (keep >> 53) {  // rounded up to the next power of two
-        keep >>= 1;
-        msb++;
-    }
-    const int ex = msb + e;
-    if (ex < -1022 || ex > 1023) return ldexp(static_cast<double>(T), e);
-    return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(ex + 1023) << 52) |
-                                                       (keep & ((1ull << 52) - 1))));
-}
-// x rounded to the nearest float (ties to even), as __double2float_rn(x),
-// with integer operations; zero, subnormal, overflowing and non-finite
-// inputs take the library path.
-__device__ __forceinline__ float f64_to_f32_rn(double x)
-{
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const int ex = int((b >> 52) & 0x7FF) - 1023;
-    if (ex < -126 || ex > 127) return __double2float_rn(x);
-    const unsigned long long mant = b & ((1ull << 52) - 1);
-    unsigned int keep = static_cast<unsigned int>(mant >> 29);
-    const unsigned long long rem = mant & ((1ull << 29) - 1);
-    if (rem > (1ull << 28) || (rem == (1ull << 28) && (keep & 1u))) keep++;
-    // a carry out of the mantissa moves into the exponent field, as it must
-    const unsigned int fb = static_cast<unsigned int>((b >> 32) & 0x80000000ull) |
-                            (static_cast<unsigned int>(ex + 127) << 23);
-    return __uint_as_float(fb + keep);
-}
 
 // R(i,j) -= T(i,j) 2^(e_i + f_j - W) for the rows i >= row_lo the tensor-core
 // launch over K range [k_lo, k_hi) reached; for the rows of that range it
 // also subtracts the diagonal part Mv(i,i) D(i,j), D(i,j) = z(i,j) 2^(f_j-16)
 // with z = 256 z_1 + z_2 the correction digits (exact), in one FMA, and
 // writes Y = float(R) for the next low-precision solve (the launch holding
-// row i is the last to touch it).  One thread per element, 256 rows x 1
-// column per CTA (grid: columns x row chunks).
-__global__ void __launch_bounds__(256)
+// row i is the last to touch it).  One column per CTA row of the grid, each
+// warp 128 rows, 4 lane-contiguous rows per thread (coalesced, with four
+// independent element updates in flight per thread).
+__global__ void __launch_bounds__(256, 5)
 residual_apply_kernel(double *R, const long long *Tg, const int *e_row, const int *f_col, int W, const double *dg,
                       const __nv_bfloat16 *Zs, float *Y, int64_t kp, int64_t np, int64_t row_lo, int64_t k_lo,
                       int64_t k_hi)
 {
-    const int64_t i = row_lo + int64_t(blockIdx.y) * 256 + threadIdx.x;
     const int64_t j = blockIdx.x;
-    if (i >= kp) return;
-    const int64_t o = i + j * kp;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ib = row_lo + (int64_t(blockIdx.y) * 8 + warp) * 128 + lane;
     const int fj = f_col[j];
-    double v = R[o] - scaled_i64_to_f64(Tg[o], e_row[i] - W + fj);
-    if (i >= k_lo && i < k_hi) {
-        const int z = __bfloat162int_rn(Zs[o]) * 256 + __bfloat162int_rn(Zs[np * kp + o]);
-        v = fma(-dg[i], scaled_i32_to_f64(z, fj - 16), v);
-        Y[o] = f64_to_f32_rn(v);
+    const int64_t o0 = ib + j * kp;
+    // every load of the thread first
+    double r[4], d[4];
+    long long tv[4];
+    int e[4];
+    __nv_bfloat16 z1[4], z2[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int64_t i = ib + 32 * q, o = o0 + 32 * q;
+        const bool in = i < kp, ink = in && i >= k_lo && i < k_hi;
+        r[q] = in ? R[o] : 0.0;
+        tv[q] = in ? Tg[o] : 0ll;
+        e[q] = in ? e_row[i] : 0;
+        d[q] = ink ? dg[i] : 0.0;
+        z1[q] = ink ? Zs[o] : __ushort_as_bfloat16(0);
+        z2[q] = ink ? Zs[np * kp + o] : __ushort_as_bfloat16(0);
     }
-    R[o] = v;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int64_t i = ib + 32 * q, o = o0 + 32 * q;
+        if (i < kp) {
+            double v = r[q] - scaled_i64_to_f64(tv[q], e[q] - W + fj);
+            if (i >= k_lo && i < k_hi) {
+                v = fma(-d[q], scaled_i32_to_f64(digit_pair(z1[q], z2[q]), fj - 16), v);
+                Y[o] = f64_to_f32_rn(v);
+            }
+            R[o] = v;
+        }
+    }
 }
 
 // ---- workspace --------------------------------------------------------------
@@ -605,7 +982,7 @@ int residual_update(double *R, long long *Tg, const __nv_bfloat16 *As, const __n
         int64_t hi = lo + 16384 < kp ? lo + 16384 : kp;
         GB_TRY(launch_tc_residual(Tg, kp, As, Zs, kp, np, lo, hi, P, P2, s, status_word));
         LaunchScope ls(KK_CONVERT, s, 0, 30.0 * double(kp - lo) * double(np));
-        const dim3 grid((unsigned)np, (unsigned)((kp - lo + 255) / 256));
+        const dim3 grid((unsigned)np, (unsigned)((kp - lo + 1023) / 1024));
         residual_apply_kernel<<<grid, 256, 0, s>>>(R, Tg, e_row, f_col, W, dg, Zs, Y, kp, np, lo, lo, hi);
         GB_TRY(check(cudaGetLastError()));
     }
@@ -710,6 +1087,7 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec)
     L.o_norm = take(64);
     L.o_dg = take(size_t(L.kp) * 8);
     L.o_xm = take(size_t(L.np) * 4);
+    L.o_cs = take(size_t(L.np) * 4);
     if (prec == GB_PREC_FP8) {
         const size_t nbk = size_t(L.kp / 128);
         L.o_a8 = take(kk);
@@ -730,7 +1108,7 @@ struct MixedBufs {
     float *band, *binv, *Y, *xmax;
     double *R, *X, *norms, *dg;
     long long *Tg;
-    int *e_row, *f_col;
+    int *e_row, *f_col, *cs;
     uint8_t *A8, *Y8;
     unsigned *bmax;
     float *bscale, *sY;
@@ -748,6 +1126,7 @@ static MixedBufs mixed_bufs(const MixedLayout &L, char *ws, bool fp8)
     b.binv = reinterpret_cast<float *>(ws + L.o_binv);
     b.Y = reinterpret_cast<float *>(ws + L.o_y);
     b.xmax = reinterpret_cast<float *>(ws + L.o_xm);
+    b.cs = reinterpret_cast<int *>(ws + L.o_cs);
     b.R = reinterpret_cast<double *>(ws + L.o_r);
     b.X = reinterpret_cast<double *>(ws + L.o_x);
     b.norms = reinterpret_cast<double *>(ws + L.o_norm);
@@ -839,8 +1218,11 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
         if (b_ready && (st = check(cudaStreamWaitEvent(s, b_ready, 0)))) break;
         {
             LaunchScope ls(KK_CONVERT, s, 0, 16.0 * double(kp) * double(np));
-            prepB_kernel<<<dim3((unsigned)(np / 64), (unsigned)(kp / 64)), 256, 0, s>>>(
-                B, ldb, side == GB_LEFT, !forward, k, ncols, alpha, R, Y, kp);
+            int ea = 0;
+            const double am = 2.0 * std::frexp(alpha, &ea);  // alpha = am 2^(ea - 1), 1 <= |am| < 2
+            ea -= 1;
+            if ((st = launch_prepB(B, ldb, side == GB_LEFT, !forward, k, ncols, am, ea, R, Y, bf.cs, kp, np, s)))
+                break;
             if ((st = check(cudaGetLastError()))) break;
         }
         LowExec le{Y, Ybf, Abf, binv, kp, np, s, status_word};
@@ -883,8 +1265,7 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
             }
             {
                 LaunchScope ls(KK_CONVERT, s, 0, (folded ? 24.0 : 8.0) * double(nel));
-                slice_cols_kernel<<<(unsigned)np, 256, 0, s>>>(Y, kp, np, ncols, Zc, fc, folded ? X : nullptr,
-                                                                xmax, norms, t == 0);
+                launch_slice_cols(Y, kp, np, ncols, Zc, fc, folded ? X : nullptr, xmax, norms, t == 0, s);
                 if ((st = check(cudaGetLastError()))) break;
             }
             nz = folded ? 0 : t + 1;
@@ -932,8 +1313,12 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
         if (st) break;
         {
             LaunchScope ls(KK_CONVERT, s, 0, 16.0 * double(k) * double(ncols));
-            writeback_kernel<<<dim3((unsigned)(np / 64), (unsigned)(kp / 64)), 256, 0, s>>>(
-                Bout, ldbo, side == GB_LEFT, !forward, k, ncols, X, kp, np, Zs, f_col, nz);
+            if (side == GB_LEFT)
+                writeback_left_kernel<<<dim3((unsigned)ncols, (unsigned)((k + 1023) / 1024)), 256, 0, s>>>(
+                    Bout, ldbo, !forward, k, X, kp, np, Zs, f_col, nz, bf.cs);
+            else
+                writeback_kernel<<<dim3((unsigned)(np / 64), (unsigned)(kp / 64)), 256, 0, s>>>(
+                    Bout, ldbo, false, !forward, k, ncols, X, kp, np, Zs, f_col, nz, bf.cs);
             if ((st = check(cudaGetLastError()))) break;
         }
     } while (0);

@@ -11,7 +11,7 @@ namespace gb {
 // right-hand sides padded to multiples of 128 as kp, np); `total` bytes.
 struct MixedLayout {
     int64_t kp, np;
-    size_t o_abf, o_as, o_band, o_binv, o_binv16, o_r, o_t, o_x, o_y, o_ybf, o_zs, o_e, o_f, o_norm, o_dg, o_xm;
+    size_t o_abf, o_as, o_band, o_binv, o_binv16, o_r, o_t, o_x, o_y, o_ybf, o_zs, o_e, o_f, o_norm, o_dg, o_xm, o_cs;
     size_t o_a8, o_bmax, o_bscale, o_y8, o_sy;  // FP8 variant only (0 otherwise)
     size_t total;
 };

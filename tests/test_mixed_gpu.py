@@ -124,25 +124,51 @@ def test_long_refinement_folds_kept_corrections(max_iter):
 
 
 def test_out_of_fp32_range_is_reported_not_silent():
-    """The low-precision solve works in FP32/BF16: right-hand sides beyond the
-    FP32 range (or not finite) cannot be refined, and the call says so with
-    GB_STATUS_RANGE and leaves B as it was, instead of returning a wrong X as
-    if it had converged."""
+    """The low-precision solve works in FP32/BF16 on power-of-two scaled
+    right-hand sides: a solution that grows beyond the FP32 range relative to
+    its right-hand side (here X(i) ~ 3^i from a unit triangle with -2 below
+    the diagonal), or non-finite data, cannot be refined, and the call says so
+    with GB_STATUS_RANGE and leaves B as it was, instead of returning a wrong X
+    as if it had converged."""
     import torch
     from paper_2305_19917_gb300 import api
-    A, B = inputs.make_problem(0, 0, 0, 0, 256, 16, seed=31)
-    Ad = api.to_device_colmajor(A, torch.float64)
-    for bad in (B * 1e300, np.where(np.arange(16) == 5, np.nan, B)):
+    m, n = 256, 16
+    A, B = inputs.make_problem(0, 0, 0, 0, m, n, seed=31)
+    G = np.tril(np.full((m, m), -2.0), -1) + np.eye(m)   # X(i) = 3^i B(0) for B = e_0
+    cases = [(A, np.where(np.arange(n) == 5, np.nan, B)), (G, B)]
+    for Am, bad in cases:
+        Ad = api.to_device_colmajor(Am, torch.float64)
         Bd = api.to_device_colmajor(bad, torch.float64)
-        st, it, est = api.gb_dtrsm_mixed(0, 0, 0, 0, 256, 16, 1.0, Ad.data_ptr(), 256, Bd.data_ptr(), 256, 1e-11,
+        st, it, est = api.gb_dtrsm_mixed(0, 0, 0, 0, m, n, 1.0, Ad.data_ptr(), m, Bd.data_ptr(), m, 1e-11,
                                          api.PREC_BF16, 4, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         assert st == api.STATUS_RANGE
         np.testing.assert_array_equal(Bd.cpu().numpy(), bad)
     assert "range" in api.gb_status_string(api.STATUS_RANGE)
-    # a right-hand side scaled within the FP32 range converges as usual
-    Bd = api.to_device_colmajor(B * 1e30, torch.float64)
-    st, it, est = api.trsm_mixed(0, 0, 0, 0, 1.0, Ad, Bd)
+
+
+@pytest.mark.parametrize("scale", [1e-300, 1e-310, 1e-40, 1e30, 1e300])
+@pytest.mark.parametrize("side", [0, 1])
+def test_scale_of_b_does_not_matter(scale, side):
+    """Right-hand sides far outside the FP32 range (down to FP64 subnormals,
+    up to 1e300) and alpha far from 1 are solved to full accuracy: every
+    column is scaled by a power of two for the low-precision solve and scaled
+    back exactly.  Columns of different scales are independent."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    m, n = (200, 12) if side == 0 else (12, 200)
+    A, B = inputs.make_problem(side, 0, 0, 0, m, n, seed=32)
+    # per right-hand side: the given scale, 1, and a mix (columns for left, rows for right)
+    w = np.array([scale, 1.0, scale * 1e6 if scale < 1 else scale * 1e-6] * 4)
+    Bs = B * w[None, :] if side == 0 else B * w[:, None]
+    alpha = 2.0 ** -300 if scale > 1 else 1.0
+    Xo = oracle.dtrsm(side, 0, 0, 0, alpha, A, Bs)
+    Ad = api.to_device_colmajor(A, torch.float64)
+    Bd = api.to_device_colmajor(Bs, torch.float64)
+    st, it, est = api.trsm_mixed(side, 0, 0, 0, alpha, Ad, Bd)
     torch.cuda.synchronize()
-    Xo = oracle.dtrsm(0, 0, 0, 0, 1.0, A, B * 1e30)
-    assert st == 0 and np.linalg.norm(Bd.cpu().numpy() - Xo) <= 1e-10 * np.linalg.norm(Xo)
+    X = Bd.cpu().numpy()
+    assert st == 0, (st, it, est)
+    Xc, Oc = (X, Xo) if side == 0 else (X.T, Xo.T)
+    for j in range(Xc.shape[1]):
+        assert np.linalg.norm(Xc[:, j] - Oc[:, j]) <= 1e-10 * np.linalg.norm(Oc[:, j]), (j, w[j])
