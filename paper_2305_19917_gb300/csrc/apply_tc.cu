@@ -44,18 +44,23 @@ __device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, boo
 
 constexpr int NTH = 256;
 
-// Left-looking leaf step: for the 128-row block at b0 of a leaf that starts
-// at s0 (K = b0 - s0 rows of that leaf already solved),
+// One leaf of the low-precision solve, left-looking, in one launch: for its
+// blocks b = 0, 1, ..., nblk-1 (rows b0 = s0 + 128 b .. b0 + 127)
 //     Y_b -= L(b, s0:b0) X(s0:b0)          (BF16 tensor cores, FP32 in TMEM)
 //     X_b  = L_b^-1 Y_b                    (two-term BF16 split, as above)
-// in one kernel per 128-column panel: the Y_b panel is read once and X_b
-// written once, instead of a GEMM launch that rewrites Y_b in memory and a
-// TS launch that reads it back.  The GEMM operands stream through a 3-stage
-// TMA ring (A rows of the BF16 copy of Mv, X's BF16 copy), the FP32 panel
-// and the inverse's two terms arrive meanwhile; the ring then holds the split
-// panel.  Thread 0 issues TMA, thread 32 the MMAs; all 8 warps do the
-// subtraction, the split and the stores (warps w, w+4 share TMEM lanes
-// 32(w%4).. and split the columns).
+// One CTA per 128-column panel walks the blocks in order: the columns of
+// the right-hand side are independent, so a panel needs only its own X of
+// the earlier blocks, which it wrote itself (stores, then a proxy fence
+// before the tensor-memory-access reads of them) -- no launch, prologue or
+// grid-wide wait between blocks.  Per block: the GEMM operands stream
+// through a 3-stage TMA ring (A rows of the BF16 copy of Mv, X's BF16 copy;
+// the ring position runs on across blocks), the FP32 panel and the
+// inverse's two terms arrive meanwhile, the ring then holds the split panel.
+// While a block's X is stored, the next block's FP32 panel, inverse and
+// first k-tiles (those not needing that X) are already on their way.
+// Thread 0 issues TMA, thread 32 the MMAs; all 8 warps do the subtraction,
+// the split and the stores (warps w, w+4 share TMEM lanes 32(w%4).. and
+// split the columns).
 constexpr int LST = 3;                                  // ring stages
 constexpr uint32_t LA_BYTES = TB * 64 * 2;              // 128 rows x 64 K of A
 constexpr uint32_t LB_BYTES = TB * 64 * 2;              // 128 columns x 64 K of X
@@ -64,10 +69,9 @@ static_assert(LST * LSTAGE >= 2 * OP_BYTES, "the ring holds the split panel afte
 constexpr size_t LEAF_SMEM = 1024 + LST * size_t(LSTAGE) + PANEL_BYTES + 2 * size_t(OP_BYTES) + 256;
 
 __global__ void __launch_bounds__(NTH, 1)
-leaf_step_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
-                    const __grid_constant__ CUtensorMap tmL, int b0, int s0, int K, int lo_row,
-                    float *__restrict__ Y, int64_t ldy, __nv_bfloat16 *__restrict__ Ybf, int64_t ncols,
-                    int *status)
+leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
+               const __grid_constant__ CUtensorMap tmL, int s0, int nblk, int kp, float *__restrict__ Y,
+               int64_t ldy, __nv_bfloat16 *__restrict__ Ybf, int64_t ncols, int *status)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -80,7 +84,6 @@ leaf_step_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t c0 = int64_t(blockIdx.x) * TB;
-    const int nk = K / 64;
     tc::pdl_launch_dependents();
 
     if (tid == 0) {
@@ -101,130 +104,168 @@ leaf_step_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     const uint32_t tmem = tslot;
     volatile int *ab = &abort_flag;
     tc::pdl_wait();  // Y, its BF16 copy: the previous kernel's until it completes
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
+    uint32_t g = 0;  // ring position (k-tiles issued so far)
+    int pre = 0;     // thread 0: k-tiles of the current block issued during the previous one
 
-    // the FP32 panel of Y_b, every copy in flight at once
-    for (int idx = tid; idx < TB * TB / 4; idx += NTH) {
-        const int j = idx >> 5, k4 = (idx & 31) * 4;
-        const int64_t col = c0 + j;
-        const bool in = col < ncols;
-        cp_async16_zfill(sP + j * TB + k4, in ? Y + b0 + k4 + col * ldy : Y, in);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-
-    if (tid == 0) {
-        tc::tma_prefetch_desc(&tmL);
+    // the FP32 panel of Y_b (rows b0..), every copy in flight at once
+    auto load_panel = [&](int b0) {
+        for (int idx = tid; idx < TB * TB / 4; idx += NTH) {
+            const int j = idx >> 5, k4 = (idx & 31) * 4;
+            const int64_t col = c0 + j;
+            const bool in = col < ncols;
+            cp_async16_zfill(sP + j * TB + k4, in ? Y + b0 + k4 + col * ldy : Y, in);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // thread 0: the inverse's two terms for block b0
+    auto load_inverse = [&](int b0) {
         tc::mbar_arrive_expect_tx(&bar_l, 2 * OP_BYTES);
         tc::tma_load_2d(&tmL, &bar_l, sLh, 0, b0);
         tc::tma_load_2d(&tmL, &bar_l, sLh + HALF_BYTES, 64, b0);
-        tc::tma_load_2d(&tmL, &bar_l, sLl, 0, lo_row);
-        tc::tma_load_2d(&tmL, &bar_l, sLl + HALF_BYTES, 64, lo_row);
-        for (int kt = 0; kt < nk; kt++) {
-            const int st = kt % LST;
-            const uint32_t ph = (kt / LST) & 1;
-            if (!tc::mbar_wait(&empty[st], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) break;
-            tc::mbar_arrive_expect_tx(&full[st], LSTAGE);
-            tc::tma_load_2d(&tmA, &full[st], ring + st * LSTAGE, s0 + kt * 64, b0);
-            tc::tma_load_2d(&tmX, &full[st], ring + st * LSTAGE + LA_BYTES, s0 + kt * 64, int(c0));
-        }
-    } else if (tid == 32) {
-        constexpr uint32_t idesc = tc::idesc_bf16_f32(TB, TB);
-        for (int kt = 0; kt < nk; kt++) {
-            const int st = kt % LST;
-            const uint32_t ph = (kt / LST) & 1;
-            if (!tc::mbar_wait(&full[st], ph, ab, status, tc::TC_TIMEOUT_MMA)) break;
-            tc::tc_fence_after();
-            const uint32_t a0 = tc::smem_u32(ring + st * LSTAGE), x0 = a0 + LA_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < 4; kk++)
-                tc::mma_f16(tmem, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(x0 + kk * 32), idesc,
-                            (kt | kk) != 0);
-            tc::mma_commit(&empty[st]);
-        }
-        tc::mma_commit(&bar_g);  // also when nk == 0: arrives at once
+        tc::tma_load_2d(&tmL, &bar_l, sLl, 0, kp + b0);
+        tc::tma_load_2d(&tmL, &bar_l, sLl + HALF_BYTES, 64, kp + b0);
+    };
+    // thread 0: k-tile kt of the GEMM of block b0 into ring position gi
+    auto load_ktile = [&](uint32_t gi, int kt, int b0) -> bool {
+        const int st = int(gi % LST);
+        const uint32_t phs = (gi / LST) & 1u;
+        if (!tc::mbar_wait(&empty[st], phs ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) return false;
+        tc::mbar_arrive_expect_tx(&full[st], LSTAGE);
+        tc::tma_load_2d(&tmA, &full[st], ring + st * LSTAGE, s0 + kt * 64, b0);
+        tc::tma_load_2d(&tmX, &full[st], ring + st * LSTAGE + LA_BYTES, s0 + kt * 64, int(c0));
+        return true;
+    };
+    load_panel(s0);
+    if (tid == 0) {
+        tc::tma_prefetch_desc(&tmL);
+        load_inverse(s0);
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-    const int q = warp & 3, half = warp >> 2;
-    const int r = q * 32 + lane;
-    // Y_b - L(b, s0:b0) X(s0:b0), in place in the panel
-    const bool ok_g = tc::mbar_wait(&bar_g, 0, ab, status, tc::TC_TIMEOUT_EPILOGUE);
-    if (ok_g && nk > 0) {
-        tc::tc_fence_after();
-#pragma unroll 1
-        for (int cc = half * (TB / 2); cc < (half + 1) * (TB / 2); cc += 32) {
-            uint32_t x[32];
-            tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(cc), x);
-            tc::tmem_ld_wait();
-#pragma unroll
-            for (int e = 0; e < 32; e++) sP[(cc + e) * TB + r] -= __uint_as_float(x[e]);
-        }
-    }
-    tc::tc_fence_before();
-    __syncthreads();  // the panel is complete and the ring is free (all MMAs of the GEMM are done)
-    for (int task = tid; task < TB * 16; task += NTH) {
-        const int j = task >> 4, k0 = (task & 15) * 8;
-        const float4 a = *reinterpret_cast<const float4 *>(sP + j * TB + k0);
-        const float4 b = *reinterpret_cast<const float4 *>(sP + j * TB + k0 + 4);
-        const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v[e], v[e + 1]);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(v[e] - __low2float(h), v[e + 1] - __high2float(h));
-            hw[e / 2] = *reinterpret_cast<const uint32_t *>(&h);
-            lw[e / 2] = *reinterpret_cast<const uint32_t *>(&l);
-        }
-        const uint32_t off = sw128_off(j, k0);
-        *reinterpret_cast<uint4 *>(sYh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4 *>(sYl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 32) {
-        if (ok_g && tc::mbar_wait(&bar_l, 0, ab, status, tc::TC_TIMEOUT_MMA)) {
-            tc::tc_fence_after();
+
+    for (int blk = 0; blk < nblk; blk++) {
+        const int b0 = s0 + blk * TB, nk = blk * (TB / 64);
+        const uint32_t ph = uint32_t(blk) & 1u;
+        if (tid == 0) {
+            for (int kt = pre; kt < nk; kt++)
+                if (!load_ktile(g + uint32_t(kt), kt, b0)) break;
+        } else if (tid == 32) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(TB, TB);
-            const uint8_t *As[3] = {sLh, sLh, sLl};
-            const uint8_t *Bs[3] = {sYh, sYl, sYh};
-            uint32_t acc = 0;
+            for (int kt = 0; kt < nk; kt++) {
+                const uint32_t gi = g + uint32_t(kt);
+                const int st = int(gi % LST);
+                const uint32_t phs = (gi / LST) & 1u;
+                if (!tc::mbar_wait(&full[st], phs, ab, status, tc::TC_TIMEOUT_MMA)) break;
+                tc::tc_fence_after();
+                const uint32_t a0 = tc::smem_u32(ring + st * LSTAGE), x0 = a0 + LA_BYTES;
 #pragma unroll
-            for (int pr = 0; pr < 3; pr++) {
-                const uint32_t a0 = tc::smem_u32(As[pr]), y0 = tc::smem_u32(Bs[pr]);
-#pragma unroll
-                for (int kk = 0; kk < TB / 16; kk++) {
-                    const uint32_t o = uint32_t(kk >> 2) * HALF_BYTES + uint32_t(kk & 3) * 32u;
-                    tc::mma_f16(tmem + TB, tc::desc_kmajor_sw128(a0 + o), tc::desc_kmajor_sw128(y0 + o), idesc,
-                                acc);
-                    acc = 1;
-                }
+                for (int kk = 0; kk < 4; kk++)
+                    tc::mma_f16(tmem, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(x0 + kk * 32), idesc,
+                                (kt | kk) != 0);
+                tc::mma_commit(&empty[st]);
             }
+            tc::mma_commit(&bar_g);  // also when nk == 0: arrives once the earlier MMAs are done
         }
-        tc::mma_commit(&bar_x);
-    }
-    if (tc::mbar_wait(&bar_x, 0, ab, status, tc::TC_TIMEOUT_EPILOGUE) && !*ab) {
-        tc::tc_fence_after();
+        g += uint32_t(nk);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        // Y_b - L(b, s0:b0) X(s0:b0), in place in the panel
+        const bool ok_g = tc::mbar_wait(&bar_g, ph, ab, status, tc::TC_TIMEOUT_EPILOGUE);
+        if (ok_g && nk > 0) {
+            tc::tc_fence_after();
 #pragma unroll 1
-        for (int cc = half * (TB / 2); cc < (half + 1) * (TB / 2); cc += 32) {
-            uint32_t x[32];
-            tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(TB + cc), x);
-            tc::tmem_ld_wait();
+            for (int cc = half * (TB / 2); cc < (half + 1) * (TB / 2); cc += 32) {
+                uint32_t x[32];
+                tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(cc), x);
+                tc::tmem_ld_wait();
 #pragma unroll
-            for (int e = 0; e < 32; e++) {
-                const int64_t col = c0 + cc + e;
-                if (col < ncols) {
-                    const float val = __uint_as_float(x[e]);
-                    Y[b0 + r + col * ldy] = val;
-                    Ybf[b0 + r + col * ldy] = __float2bfloat16_rn(val);
+                for (int e = 0; e < 32; e++) sP[(cc + e) * TB + r] -= __uint_as_float(x[e]);
+            }
+        }
+        tc::tc_fence_before();
+        __syncthreads();  // the panel is complete and the ring is free (all MMAs of the GEMM are done)
+        for (int task = tid; task < TB * 16; task += NTH) {
+            const int j = task >> 4, k0 = (task & 15) * 8;
+            const float4 a = *reinterpret_cast<const float4 *>(sP + j * TB + k0);
+            const float4 b = *reinterpret_cast<const float4 *>(sP + j * TB + k0 + 4);
+            const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v[e], v[e + 1]);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(v[e] - __low2float(h), v[e + 1] - __high2float(h));
+                hw[e / 2] = *reinterpret_cast<const uint32_t *>(&h);
+                lw[e / 2] = *reinterpret_cast<const uint32_t *>(&l);
+            }
+            const uint32_t off = sw128_off(j, k0);
+            *reinterpret_cast<uint4 *>(sYh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(sYl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (blk + 1 < nblk) load_panel(b0 + TB);  // the panel is free again: the next block's
+        if (tid == 32) {
+            if (ok_g && tc::mbar_wait(&bar_l, ph, ab, status, tc::TC_TIMEOUT_MMA)) {
+                tc::tc_fence_after();
+                constexpr uint32_t idesc = tc::idesc_bf16_f32(TB, TB);
+                const uint8_t *As[3] = {sLh, sLh, sLl};
+                const uint8_t *Bs[3] = {sYh, sYl, sYh};
+                uint32_t acc = 0;
+#pragma unroll
+                for (int pr = 0; pr < 3; pr++) {
+                    const uint32_t a0 = tc::smem_u32(As[pr]), y0 = tc::smem_u32(Bs[pr]);
+#pragma unroll
+                    for (int kk = 0; kk < TB / 16; kk++) {
+                        const uint32_t o = uint32_t(kk >> 2) * HALF_BYTES + uint32_t(kk & 3) * 32u;
+                        tc::mma_f16(tmem + TB, tc::desc_kmajor_sw128(a0 + o), tc::desc_kmajor_sw128(y0 + o), idesc,
+                                    acc);
+                        acc = 1;
+                    }
+                }
+            }
+            tc::mma_commit(&bar_x);
+        }
+        const bool ok_x = tc::mbar_wait(&bar_x, ph, ab, status, tc::TC_TIMEOUT_EPILOGUE);
+        pre = 0;
+        if (ok_x && tid == 0 && blk + 1 < nblk) {
+            // the split panel and the inverse are consumed: the next block's
+            // inverse, and its first k-tiles that do not need this block's X
+            // (rows below b0), go out while this block's X is stored
+            load_inverse(b0 + TB);
+            const int nkn = (blk + 1) * (TB / 64);
+            pre = min(LST, nkn - TB / 64);
+            for (int kt = 0; kt < pre; kt++)
+                if (!load_ktile(g + uint32_t(kt), kt, b0 + TB)) {
+                    pre = nkn;  // stop issuing: the wait has timed out and set the abort flag
+                    break;
+                }
+        }
+        if (ok_x && !*ab) {
+            tc::tc_fence_after();
+#pragma unroll 1
+            for (int cc = half * (TB / 2); cc < (half + 1) * (TB / 2); cc += 32) {
+                uint32_t x[32];
+                tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(TB + cc), x);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int e = 0; e < 32; e++) {
+                    const int64_t col = c0 + cc + e;
+                    if (col < ncols) {
+                        const float val = __uint_as_float(x[e]);
+                        Y[b0 + r + col * ldy] = val;
+                        Ybf[b0 + r + col * ldy] = __float2bfloat16_rn(val);
+                    }
                 }
             }
         }
+        // X_b's BF16 copy is read by the tensor memory accesses of the next blocks
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        tc::tc_fence_before();
+        __syncthreads();
+        if (*ab) break;
     }
-    tc::tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, 2 * TB);
-    }
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * TB);
 }
 
 }  // namespace
@@ -233,24 +274,23 @@ int apply_tc_prepare()
 {
     static bool attr = false;
     if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(leaf_step_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)LEAF_SMEM));
+        GB_CUDA(cudaFuncSetAttribute(leaf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM));
         attr = true;
     }
     return device_status_word() ? 0 : GB_STATUS_CUDA_ERROR;
 }
 
-// Left-looking leaf step of the low-precision solve on block b0 (a multiple
-// of 128) of a leaf starting at s0 <= b0: Y(b0:b0+128, :) -= Mv(b0.., s0:b0)
-// X(s0:b0, :), then X_b = L_b^-1 Y_b (FP32 and BF16 copies), over all np
-// columns.  Abf: BF16 Mv, row-major, leading dimension kp; Y / Ybf: the FP32
-// right-hand side and its BF16 copy (column-major, kp); inv16: the inverses'
-// high terms in rows b*128.., their low terms in rows kp + b*128.. (128 wide).
-int launch_leaf_step_tc(const __nv_bfloat16 *Abf, const __nv_bfloat16 *inv16, int64_t kp, int64_t np, int64_t b0,
-                        int64_t s0, float *Y, __nv_bfloat16 *Ybf, cudaStream_t s, int *status)
+// One leaf of the low-precision solve: rows s0 .. s0 + nr - 1 (s0 and nr
+// multiples of 128), every 128-row block updated from the leaf's solved
+// blocks and solved with its inverse, over all np columns.  Abf: BF16 Mv,
+// row-major, leading dimension kp; Y / Ybf: the FP32 right-hand side and its
+// BF16 copy (column-major, kp); inv16: the inverses' high terms in rows
+// b*128.., their low terms in rows kp + b*128.. (128 wide).
+int launch_leaf_tc(const __nv_bfloat16 *Abf, const __nv_bfloat16 *inv16, int64_t kp, int64_t np, int64_t s0,
+                   int64_t nr, float *Y, __nv_bfloat16 *Ybf, cudaStream_t s, int *status)
 {
-    if (np <= 0) return 0;
-    if (kp % TB || np % TB || b0 % TB || s0 % TB || s0 > b0 || b0 + TB > kp || 2 * kp > 0x7fffffffLL ||
+    if (np <= 0 || nr <= 0) return 0;
+    if (kp % TB || np % TB || s0 % TB || nr % TB || s0 + nr > kp || 2 * kp > 0x7fffffffLL ||
         (reinterpret_cast<uintptr_t>(Y) & 15) || (reinterpret_cast<uintptr_t>(Abf) & 15) ||
         (reinterpret_cast<uintptr_t>(Ybf) & 15) || (reinterpret_cast<uintptr_t>(inv16) & 15))
         return GB_STATUS_CUDA_ERROR;
@@ -276,11 +316,12 @@ int launch_leaf_step_tc(const __nv_bfloat16 *Abf, const __nv_bfloat16 *inv16, in
     GB_TRY(apply_tc_prepare());
     int *st = status ? status : device_status_word();
     if (!st) return GB_STATUS_CUDA_ERROR;
-    const double K = double(b0 - s0);
-    LaunchScope ls(KK_DIAG, s, (2.0 * TB * K + 3.0 * 2.0 * TB * TB) * double(np),
-                   2.0 * TB * K + 2.0 * K * np + 10.0 * TB * double(np));
-    return check(launch_pdl(leaf_step_tc_kernel, dim3((unsigned)(np / TB)), dim3(NTH), LEAF_SMEM, s, ta, tx, tl,
-                            int(b0), int(s0), int(b0 - s0), int(kp + b0), Y, kp, Ybf, np, st));
+    const double nrd = double(nr);
+    // GEMM flops of the leaf (sum over blocks of 2 * 128 * K * np) plus the 3 split products per block
+    LaunchScope ls(KK_DIAG, s, (nrd * (nrd - TB) + 3.0 * 2.0 * TB * nrd) * double(np),
+                   nrd * nrd + nrd * (nrd - TB) / TB * double(np) + 10.0 * nrd * double(np));
+    return check(launch_pdl(leaf_tc_kernel, dim3((unsigned)(np / TB)), dim3(NTH), LEAF_SMEM, s, ta, tx, tl, int(s0),
+                            int(nr / TB), int(kp), Y, kp, Ybf, np, st));
 }
 
 }  // namespace gb

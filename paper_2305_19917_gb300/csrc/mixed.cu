@@ -47,8 +47,8 @@ int launch_apply_inverse_fp8(const float *Linv_b, float *Yb, int64_t ldy, uint8_
 int diag_inv_prepare();
 int launch_invert_blocks(const float *band, float *inv, __nv_bfloat16 *inv16, int64_t nblocks, cudaStream_t s);
 int apply_tc_prepare();
-int launch_leaf_step_tc(const __nv_bfloat16 *Abf, const __nv_bfloat16 *inv16, int64_t kp, int64_t np, int64_t b0,
-                        int64_t s0, float *Y, __nv_bfloat16 *Ybf, cudaStream_t s, int *status);
+int launch_leaf_tc(const __nv_bfloat16 *Abf, const __nv_bfloat16 *inv16, int64_t kp, int64_t np, int64_t s0,
+                   int64_t nr, float *Y, __nv_bfloat16 *Ybf, cudaStream_t s, int *status);
 namespace {
 
 constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
@@ -907,11 +907,10 @@ struct LowExec {
     {
         if (status) return;
         if (!fp8) {
-            // BF16 form: a leaf of up to kLeaf rows, left-looking: each
-            // 128-row block takes its update from the solved blocks of the
-            // leaf and its TS task in one fused kernel
-            for (int64_t blk = b0; blk < b0 + nr && !status; blk += kBand)
-                status = launch_leaf_step_tc(Abf, binv16, kp, np, blk, b0, Y, Ybf, s, status_word);
+            // BF16 form: a leaf of up to kLeaf rows, left-looking, in one
+            // launch: each 128-row block takes its update from the solved
+            // blocks of the leaf and its TS task
+            status = launch_leaf_tc(Abf, binv16, kp, np, b0, nr, Y, Ybf, s, status_word);
             return;
         }
         if (nr > kBand) {
