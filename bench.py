@@ -317,12 +317,13 @@ def run_ours(args):
         A_e = api.colmajor_empty(m, m, torch.float64)
         h2d, d2h = (m * m + m * n) * 8, m * n * 8
     if mixed:
-        # one untimed call: the host entry point solves in column blocks, whose
-        # low-precision solve graph is captured on first use
-        B_pin.copy_(B_host0)
-        api.trsm_mixed_host(side, uplo, trans, diag, alpha, A_pin, B_pin, tol=tol, prec=prec, max_iter=max_iter,
-                            stream=stream)
-    for _ in range(max(1, min(args.steps, 2))):
+        # two untimed calls: the host entry point solves in column blocks, whose
+        # low-precision solve graph is captured and whose buffers are mapped on first use
+        for _ in range(2):
+            B_pin.copy_(B_host0)
+            api.trsm_mixed_host(side, uplo, trans, diag, alpha, A_pin, B_pin, tol=tol, prec=prec,
+                                max_iter=max_iter, stream=stream)
+    for _ in range(max(1, min(args.steps, 3))):
         B_pin.copy_(B_host0)  # fresh right-hand sides (host copy, not timed)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()

@@ -988,30 +988,41 @@ int residual_update(double *R, long long *Tg, const __nv_bfloat16 *As, const __n
     return 0;
 }
 
-// The low-precision solve is a fixed sequence of ~2 kp/64 launches on
-// fixed buffers: it is captured once into a CUDA graph (on a library stream)
-// and replayed on the caller's stream at every refinement step.  The last
-// graph is kept per device, keyed by workspace address and sizes.
+// The low-precision solve is a fixed sequence of launches on fixed buffers:
+// it is captured once into a CUDA graph (on a library stream) and replayed
+// on the caller's stream at every refinement step.  The last few graphs are
+// kept per device (least recently used first out), keyed by work-space
+// address and sizes, so that callers alternating between problems or entry
+// points (device buffers, host buffers in column blocks) do not recapture.
 struct LowGraph {
     cudaGraphExec_t exec = nullptr;
     const void *ws = nullptr;
     int64_t kp = 0, np = 0;
     bool fp8 = false;
     uint64_t nkernels = 0;
+    uint64_t used = 0;  // last use (LRU clock)
 };
+constexpr int kGraphs = 4;
 
 int low_graph(LowExec &le, const void *ws, LowGraph **out)
 {
-    static LowGraph cache[64];
+    static LowGraph cache[64][kGraphs];
+    static uint64_t clock[64] = {0};
     static cudaStream_t cap_stream[64] = {nullptr};
     int dev = 0;
     GB_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return GB_STATUS_CUDA_ERROR;
-    LowGraph &g = cache[dev];
-    if (g.exec && g.ws == ws && g.kp == le.kp && g.np == le.np && g.fp8 == le.fp8) {
-        *out = &g;
-        return 0;
+    int victim = 0;
+    for (int i = 0; i < kGraphs; i++) {
+        LowGraph &c = cache[dev][i];
+        if (c.exec && c.ws == ws && c.kp == le.kp && c.np == le.np && c.fp8 == le.fp8) {
+            c.used = ++clock[dev];
+            *out = &c;
+            return 0;
+        }
+        if (!c.exec || (cache[dev][victim].exec && c.used < cache[dev][victim].used)) victim = i;
     }
+    LowGraph &g = cache[dev][victim];
     if (g.exec) {
         cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
@@ -1044,6 +1055,7 @@ int low_graph(LowExec &le, const void *ws, LowGraph **out)
     g.np = le.np;
     g.fp8 = le.fp8;
     g.nkernels = capture_count() - before;
+    g.used = ++clock[dev];
     *out = &g;
     return 0;
 }
