@@ -148,7 +148,10 @@ enum { GB_PREC_BF16 = 0, GB_PREC_FP8 = 1 };
  * call returns GB_STATUS_RANGE with B unchanged.
  * Synchronous: returns after the solve is complete.  Work space (about
  * 14 k^2 + 42 k n bytes, k and n rounded up to multiples of 128) comes from a
- * library-owned stream-ordered pool.
+ * library-owned stream-ordered pool.  The low-precision solve is replayed
+ * from a CUDA graph cached per device (the 4 most recently used problem
+ * shapes and work spaces); calls on one device from several host threads are
+ * serialised while they use it.
  */
 int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
                    int64_t n, double alpha, const double *A, int64_t lda,

@@ -23,6 +23,7 @@
 // diagonal, zero right-hand sides), so every tile is aligned for TMA.
 #include <cmath>
 #include <algorithm>
+#include <mutex>
 #include <cstdio>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -59,7 +60,7 @@ constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
 // an FP64 X once and updates X in place from then on.
 constexpr int kZSlots = 3;
 constexpr int kBand = 128;     // FP32 band of diagonal 128-blocks (column-major per block)
-constexpr int kLeaf = 1024;    // leaf order of the BF16 low-precision solve (8 fused leaf steps)
+constexpr int kLeaf = 1024;    // leaf order of the BF16 low-precision solve (one leaf kernel launch each)
 
 // Library fallback of the integer-built conversions below, for results
 // outside the normal double range.  Kept out of line: inlined, the compiler
@@ -869,8 +870,10 @@ struct Workspace {
 cudaMemPool_t library_pool()
 {
     static cudaMemPool_t pool[64] = {nullptr};
+    static std::mutex mu;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
     if (!pool[dev]) {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
@@ -935,7 +938,7 @@ struct LowExec {
 };
 
 // Recursive model (Section V-A) down to leaves of kLeaf rows (BF16 form:
-// solved left-looking by fused leaf steps) or kBand rows (FP8 form).
+// each solved left-looking by one leaf kernel launch) or kBand rows (FP8 form).
 int low_solve(LowExec &e, int64_t kp)
 {
     drive_recursive(e, 0, kp, 24, (int64_t)(e.fp8 ? kBand : kLeaf), 1.0f, true);
@@ -1003,6 +1006,16 @@ struct LowGraph {
     uint64_t used = 0;  // last use (LRU clock)
 };
 constexpr int kGraphs = 4;
+
+// Solves that replay cached graphs on one device are serialised: a graph in
+// use must not be evicted (destroyed) by another host thread's solve.
+std::mutex &graph_mutex()
+{
+    static std::mutex mu[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    return mu[dev];
+}
 
 int low_graph(LowExec &le, const void *ws, LowGraph **out)
 {
@@ -1219,6 +1232,7 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
     const int hist0 = merge_hist ? tl_nhist : 0;
     int hist = 0;
     if (!merge_hist) tl_nhist = 0;
+    std::unique_lock<std::mutex> graph_lock(graph_mutex(), std::defer_lock);
 
     int st = 0;
     double h_norm[4] = {0, 0, 0, 0};
@@ -1244,7 +1258,10 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
         le.Y8 = bf.Y8;
         le.sY = bf.sY;
         LowGraph *lg = nullptr;
-        if (use_graph && (st = low_graph(le, ws, &lg))) break;
+        if (use_graph) {
+            graph_lock.lock();  // held until the solve returns
+            if ((st = low_graph(le, ws, &lg))) break;
+        }
         const int64_t nel = int64_t(kn);
         __nv_bfloat16 *Zc = Zs;  // digit slot of the current correction
         int *fc = f_col;

@@ -71,7 +71,8 @@ namespace {
 // Column blocks of the pipelined host solve.  Two halves hide half of B's
 // upload and half of X's download under computation; more blocks would hide
 // more of the link but make every launch of the low-precision solve narrower
-// (its leaf steps run one CTA per 128 columns).  Below about a gigabyte of
+// (its leaf kernel runs one CTA per 128 columns, and a leaf takes as long
+// at half the width).  Below about a gigabyte of
 // right-hand sides the launches' fixed costs outweigh what the overlap
 // saves, so one block is used.  GB_MIXED_HOST_BLOCKS (1..64) overrides the
 // choice; the blocks are whole multiples of 128 columns.

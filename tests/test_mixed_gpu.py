@@ -172,3 +172,43 @@ def test_scale_of_b_does_not_matter(scale, side):
     Xc, Oc = (X, Xo) if side == 0 else (X.T, Xo.T)
     for j in range(Xc.shape[1]):
         assert np.linalg.norm(Xc[:, j] - Oc[:, j]) <= 1e-10 * np.linalg.norm(Oc[:, j]), (j, w[j])
+
+
+def test_concurrent_solves_from_two_host_threads():
+    """Two host threads solving different problems on their own streams at
+    the same time (the binding releases the interpreter lock during a call):
+    the cached low-precision graphs are shared per device, and both results
+    still match the oracle."""
+    import threading
+    import torch
+    from paper_2305_19917_gb300 import api
+    probs = [(0, 0, 0, 0, 300, 170, 1.5, 41), (1, 1, 1, 0, 96, 257, -0.5, 42)]
+    errs, fails = {}, []
+
+    def run(idx):
+        try:
+            side, uplo, trans, diag, m, n, alpha, seed = probs[idx]
+            A, B = inputs.make_problem(side, uplo, trans, diag, m, n, seed=seed)
+            Xo = oracle.dtrsm(side, uplo, trans, diag, alpha, A, B)
+            s = torch.cuda.Stream()
+            worst = 0.0
+            for _ in range(4):
+                with torch.cuda.stream(s):
+                    Ad = api.to_device_colmajor(A, torch.float64)
+                    Bd = api.to_device_colmajor(B, torch.float64)
+                s.synchronize()
+                st, it, est = api.trsm_mixed(side, uplo, trans, diag, alpha, Ad, Bd, stream=s)
+                s.synchronize()
+                assert st == 0, st
+                worst = max(worst, fwd_err(Bd.cpu().numpy(), Xo))
+            errs[idx] = worst
+        except Exception as e:  # reported below, in the main thread
+            fails.append(repr(e))
+
+    ts = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not fails, fails
+    assert errs[0] <= 1e-10 and errs[1] <= 1e-10, errs
