@@ -185,9 +185,17 @@ int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag,
  * interface addition).  Same arguments, results and status codes, except
  * that A (8) and B (10) are host pointers; X overwrites B on the host.  The
  * library copies in only the referenced triangle of A (128-column panels),
- * then B on a second stream while the kernels that need only A run, solves
- * on `stream`, and copies X back; device buffers come from its memory pool
- * and are released before it returns.  For the copies to overlap with
+ * then the right-hand sides in column blocks (columns of B for side = left,
+ * rows for right) on a second stream while the kernels that need only A
+ * run; it solves block j on `stream` while block j+1 arrives and block
+ * j-1's X goes back.  It uses two blocks once the right-hand sides reach
+ * about a gigabyte, else one; the environment variable GB_MIXED_HOST_BLOCKS
+ * (1..64) overrides the count.  Blocks are independent problems, so a
+ * block's refinement stops on its own criterion; iters_out and est_err_out
+ * report the largest over the blocks.  On an error in a later block the
+ * columns already copied back are restored: B is unchanged, as for
+ * gb_dtrsm_mixed.  Device buffers come from the library's memory pool and
+ * are released before it returns.  For the copies to overlap with
  * computation, A and B should be page-locked (cudaHostAlloc or
  * cudaHostRegister); pageable memory gives the same result, slower.
  * alpha == 0 sets B = 0 on the host without reading A.  Synchronous.
