@@ -1,8 +1,9 @@
 // Mixed-precision triangular solve with iterative refinement:
 //
 //   X0  = low-precision solve of Mv X = alpha*Bv   (BF16 tensor-core GEMM
-//         updates with FP32 accumulation, FP32 diagonal-block solves; the
-//         recursive model of Section V-A down to 64-row TS tasks)
+//         updates with FP32 accumulation; the recursive model of Section
+//         V-A down to 1024-row leaves, each solved by one tensor-core kernel
+//         launch in 128-row blocks with precomputed FP32 block inverses)
 //   repeat:  R = alpha*Bv - Mv X  (split-precision products on the tensor
 //            cores, exact integer sums, FP64 final accumulation)
 //            D = low-precision solve of Mv D = R;   X += D  (FP64)
@@ -19,7 +20,9 @@
 // Everything is done on a canonical FORWARD problem in column-major layout:
 // a backward (upper) problem is index-reversed, a right-side problem is
 // transposed, both while copying in, and the result is mapped back at the
-// end.  Sizes are padded to multiples of 128 (identity on the padded
+// end.  Each right-hand side is scaled by a power of two (exact) that brings
+// its largest entry near 1 for the FP32 / BF16 solve, and scaled back when
+// written.  Sizes are padded to multiples of 128 (identity on the padded
 // diagonal, zero right-hand sides), so every tile is aligned for TMA.
 #include <cmath>
 #include <algorithm>
@@ -55,9 +58,9 @@ namespace {
 constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
 // The corrections of the first kZSlots refinement steps are kept as their
 // digit slices (z_1, z_2 and the column exponents) and X = D_0 + D_1 + ... is
-// formed only when the solution is written back (in the same FP64 order as
-// X += D_t, so the result is identical); a longer refinement folds them into
-// an FP64 X once and updates X in place from then on.
+// formed only when the solution is written back (their exact sum, rounded
+// once); a longer refinement folds them into an FP64 X once and updates X in
+// place from then on.
 constexpr int kZSlots = 3;
 constexpr int kBand = 128;     // FP32 band of diagonal 128-blocks (column-major per block)
 constexpr int kLeaf = 1024;    // leaf order of the BF16 low-precision solve (one leaf kernel launch each)
