@@ -272,12 +272,8 @@ leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
 int apply_tc_prepare()
 {
-    static bool attr = false;
-    if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(leaf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM));
-        attr = true;
-    }
-    return device_status_word() ? 0 : GB_STATUS_CUDA_ERROR;
+    static PerDeviceOnce attr;
+    return smem_attr_once(attr, leaf_tc_kernel, LEAF_SMEM);
 }
 
 // One leaf of the low-precision solve: rows s0 .. s0 + nr - 1 (s0 and nr

@@ -316,12 +316,8 @@ int upload_and_capture(BatchedPlan &P, std::vector<Unit<T>> &units, cudaStream_t
     GB_CUDA(cudaMalloc(&P.ticket, sizeof(unsigned)));
     if (ub) GB_CUDA(cudaMemcpyAsync(P.units, units.data(), ub, cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaStreamSynchronize(s));
-    static bool attr = false;
-    if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)batched_smem<T>()));
-        attr = true;
-    }
+    static PerDeviceOnce attr;
+    GB_TRY(smem_attr_once(attr, batched_kernel<T>, batched_smem<T>()));
     int dev = 0, sms = 0, per_sm = 0;
     GB_CUDA(cudaGetDevice(&dev));
     GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

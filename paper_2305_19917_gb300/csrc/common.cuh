@@ -1,5 +1,6 @@
 // Shared definitions of the gbtrsm CUDA library (internal header).
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "../../include/gbtrsm.h"
@@ -26,6 +27,28 @@ inline int check(cudaError_t e)
     } while (0)
 
 #define GB_CUDA(expr) GB_TRY(::gb::check(expr))
+
+// One-time set-up flag per device.  Kernel attributes such as the dynamic
+// shared-memory limit belong to a device (its context): a process that
+// drives several GPUs must set them on each, so the flag is kept per device
+// (a static PerDeviceOnce starts all-clear).
+struct PerDeviceOnce {
+    std::atomic<int> done[64];
+};
+// Raise `kernel`'s dynamic shared-memory limit to `bytes` on the current
+// device, once per device (repeating it when two threads race is harmless).
+template <typename K>
+inline int smem_attr_once(PerDeviceOnce &once, K *kernel, size_t bytes)
+{
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GB_STATUS_CUDA_ERROR;
+    if (!once.done[dev].load(std::memory_order_acquire)) {
+        GB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        once.done[dev].store(1, std::memory_order_release);
+    }
+    return 0;
+}
 
 // Launch with programmatic stream serialisation: the kernel may start while
 // the previous kernel of the stream is finishing (it must execute

@@ -245,15 +245,9 @@ constexpr size_t apply_smem(int ac) { return size_t(STRIP_FLOATS) * 4 + size_t(a
 
 int diag_inv_prepare()
 {
-    static bool done = false;
-    if (!done) {
-        GB_CUDA(cudaFuncSetAttribute(invert_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)INV_SMEM));
-        GB_CUDA(cudaFuncSetAttribute(apply_inverse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)apply_smem(AC)));
-        done = true;
-    }
-    return 0;
+    static PerDeviceOnce inv_attr, apply_attr;
+    GB_TRY(smem_attr_once(inv_attr, invert_blocks_kernel, INV_SMEM));
+    return smem_attr_once(apply_attr, apply_inverse_kernel<true>, apply_smem(AC));
 }
 
 // Invert the nblocks diagonal blocks held in `band` into `inv` (strips) and,

@@ -199,14 +199,8 @@ diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
 template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT>
 int diag_prepare()
 {
-    static bool attr_done = false;  // per instantiation; idempotent if raced
-    if (!attr_done) {
-        GB_CUDA(cudaFuncSetAttribute(diag_solve_kernel<T, NB, FWD, MT, LEFT, EMIT>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)diag_smem_bytes<T, NB>()));
-        attr_done = true;
-    }
-    return 0;
+    static PerDeviceOnce attr;  // per instantiation and device
+    return smem_attr_once(attr, diag_solve_kernel<T, NB, FWD, MT, LEFT, EMIT>, diag_smem_bytes<T, NB>());
 }
 
 template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT = false>

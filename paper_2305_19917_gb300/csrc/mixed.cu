@@ -25,6 +25,7 @@
 // written.  Sizes are padded to multiples of 128 (identity on the padded
 // diagonal, zero right-hand sides), so every tile is aligned for TMA.
 #include <cmath>
+#include <cstddef>
 #include <algorithm>
 #include <mutex>
 #include <cstdio>
@@ -900,7 +901,7 @@ struct LowExec {
     const float *binv;  // inverses of the diagonal kBand-blocks
     int64_t kp, np;
     cudaStream_t s;
-    int *status_word;   // device word for wait timeouts (nullptr = library's own)
+    int *status_word;   // device word for wait timeouts
     bool fp8 = false;   // FP8 E4M3 updates with block scales instead of BF16
     const uint8_t *A8 = nullptr;
     const float *sA = nullptr;   // (kp/128)^2 block scales of A8
@@ -1111,7 +1112,7 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec)
     L.o_zs = take(kn * 4 * kZSlots);
     L.o_e = take(size_t(L.kp) * 4);
     L.o_f = take(size_t(L.np) * 4 * kZSlots);
-    L.o_norm = take(64);
+    L.o_norm = take(64);  // 4 FP64 norms, then the solve's device status word (byte 32)
     L.o_dg = take(size_t(L.kp) * 8);
     L.o_xm = take(size_t(L.np) * 4);
     L.o_cs = take(size_t(L.np) * 4);
@@ -1136,6 +1137,7 @@ struct MixedBufs {
     double *R, *X, *norms, *dg;
     long long *Tg;
     int *e_row, *f_col, *cs;
+    int *status;  // device word of this solve's bounded waits (beside the norms)
     uint8_t *A8, *Y8;
     unsigned *bmax;
     float *bscale, *sY;
@@ -1157,6 +1159,7 @@ static MixedBufs mixed_bufs(const MixedLayout &L, char *ws, bool fp8)
     b.R = reinterpret_cast<double *>(ws + L.o_r);
     b.X = reinterpret_cast<double *>(ws + L.o_x);
     b.norms = reinterpret_cast<double *>(ws + L.o_norm);
+    b.status = reinterpret_cast<int *>(ws + L.o_norm + 32);
     b.dg = reinterpret_cast<double *>(ws + L.o_dg);
     b.Tg = reinterpret_cast<long long *>(ws + L.o_t);
     b.e_row = reinterpret_cast<int *>(ws + L.o_e);
@@ -1208,8 +1211,8 @@ int mixed_prep_a(int side, int uplo, int trans, int diag, int64_t k, const doubl
 
 int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, double alpha, const double *B,
                   int64_t ldb, double *Bout, int64_t ldbo, double tol, int prec, int max_iter, int *iters_out,
-                  double *est_err_out, cudaStream_t s, char *ws, const MixedLayout &L, int *status_word,
-                  bool use_graph, cudaEvent_t b_ready, bool merge_hist)
+                  double *est_err_out, cudaStream_t s, char *ws, const MixedLayout &L, bool use_graph,
+                  cudaEvent_t b_ready, bool merge_hist)
 {
     const bool forward = mixed_forward(side, uplo, trans);
     const int64_t kp = L.kp, np = L.np;
@@ -1230,6 +1233,7 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
     auto *norms = bf.norms;
     auto *dg = bf.dg;
     auto *xmax = bf.xmax;
+    int *status_word = bf.status;
     // history of this solve: from scratch, or merged (step-wise maximum)
     // into that of the previous column block of the same problem
     const int hist0 = merge_hist ? tl_nhist : 0;
@@ -1238,10 +1242,18 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
     std::unique_lock<std::mutex> graph_lock(graph_mutex(), std::defer_lock);
 
     int st = 0;
-    double h_norm[4] = {0, 0, 0, 0};
+    // the norms of a step and the status word, read back together
+    struct StepRead {
+        double norm[4];
+        int status;
+    } h = {{0, 0, 0, 0}, 0};
+    static_assert(offsetof(StepRead, status) == 32, "status word follows the four norms");
+    double *h_norm = h.norm;
     int iters = 0;
     double est = 0;
     do {
+        // the bounded waits of this solve's kernels record timeouts here
+        if ((st = check(cudaMemsetAsync(status_word, 0, sizeof(int), s)))) break;
         // the right-hand sides may still be arriving on another stream
         if (b_ready && (st = check(cudaStreamWaitEvent(s, b_ready, 0)))) break;
         {
@@ -1300,8 +1312,14 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
                 if ((st = check(cudaGetLastError()))) break;
             }
             nz = folded ? 0 : t + 1;
-            if ((st = check(cudaMemcpyAsync(h_norm, norms, 4 * sizeof(double), cudaMemcpyDeviceToHost, s)))) break;
+            if ((st = check(cudaMemcpyAsync(&h, norms, offsetof(StepRead, status) + sizeof(int),
+                                            cudaMemcpyDeviceToHost, s))))
+                break;
             if ((st = check(cudaStreamSynchronize(s)))) break;
+            if (h.status != 0) {  // a bounded wait gave up: B is left as it was
+                st = GB_STATUS_TIMEOUT;
+                break;
+            }
             if (h_norm[3] != 0.0) {  // out of the low-precision range: B is left as it was
                 st = GB_STATUS_RANGE;
                 break;
@@ -1366,7 +1384,7 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
 
 int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
                int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
-               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph, cudaEvent_t b_ready)
+               double *est_err_out, cudaStream_t s, char *ws, bool use_graph, cudaEvent_t b_ready)
 {
     const int64_t k = side == GB_LEFT ? m : n;
     const int64_t ncols = side == GB_LEFT ? n : m;
@@ -1376,7 +1394,7 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
     if (est_err_out) *est_err_out = 0;
     GB_TRY(mixed_prep_a(side, uplo, trans, diag, k, A, lda, prec, L, ws, s));
     return mixed_solve_b(side, uplo, trans, k, ncols, alpha, B, ldb, B, ldb, tol, prec, max_iter, iters_out,
-                         est_err_out, s, ws, L, status_word, use_graph, b_ready, false);
+                         est_err_out, s, ws, L, use_graph, b_ready, false);
 }
 
 cudaMemPool_t mixed_pool() { return library_pool(); }
@@ -1391,7 +1409,7 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
     char *ws = nullptr;
     GB_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&ws), L.total, pool, s));
     const int st = mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
-                              iters_out, est_err_out, s, ws, nullptr, true, nullptr);
+                              iters_out, est_err_out, s, ws, true, nullptr);
     cudaFreeAsync(ws, s);
     return st;
 }

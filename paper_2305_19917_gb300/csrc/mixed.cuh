@@ -18,15 +18,16 @@ struct MixedLayout {
 MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec);
 
 // The refinement solve on a caller-provided work space `ws` (layout above,
-// 256-byte aligned), with `status_word` as the device word for wait
-// timeouts (nullptr = the library's own) and the low-precision solve either
-// replayed from a cached CUDA graph (use_graph) or launched directly.  With
-// b_ready, the work that reads B waits for that event (the preparation of A
-// does not).  Arguments are assumed valid; alpha != 0; m, n > 0.  Synchronous.
+// 256-byte aligned), with the low-precision solve either replayed from a
+// cached CUDA graph (use_graph) or launched directly.  The kernels' bounded
+// waits record timeouts in a status word inside the work space, cleared at
+// the start of each solve and read back at every refinement step: a timeout
+// returns GB_STATUS_TIMEOUT before anything is written to B.  With b_ready,
+// the work that reads B waits for that event (the preparation of A does
+// not).  Arguments are assumed valid; alpha != 0; m, n > 0.  Synchronous.
 int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
                int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
-               double *est_err_out, cudaStream_t s, char *ws, int *status_word, bool use_graph,
-               cudaEvent_t b_ready);
+               double *est_err_out, cudaStream_t s, char *ws, bool use_graph, cudaEvent_t b_ready);
 // The two halves of mixed_core, for callers that solve several column blocks
 // of one problem against one preparation of A (the work space laid out for
 // the widest block, L.np >= every block's ncols):
@@ -41,8 +42,8 @@ int mixed_prep_a(int side, int uplo, int trans, int diag, int64_t k, const doubl
                  const MixedLayout &L, char *ws, cudaStream_t s);
 int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, double alpha, const double *B,
                   int64_t ldb, double *Bout, int64_t ldbo, double tol, int prec, int max_iter, int *iters_out,
-                  double *est_err_out, cudaStream_t s, char *ws, const MixedLayout &L, int *status_word,
-                  bool use_graph, cudaEvent_t b_ready, bool merge_hist);
+                  double *est_err_out, cudaStream_t s, char *ws, const MixedLayout &L, bool use_graph,
+                  cudaEvent_t b_ready, bool merge_hist);
 // The library's stream-ordered memory pool for work space (current device).
 cudaMemPool_t mixed_pool();
 

@@ -187,7 +187,7 @@ extern "C" int gb_dtrsm_mixed_host(int side, int uplo, int trans, int diag, int6
             int it = 0;
             double est = 0;
             const int r = gb::mixed_solve_b(side, uplo, trans, k, w, alpha, Bd + d.off, m, out, ldo, tol, prec,
-                                            max_iter, &it, &est, s, ws, L, nullptr, true, ev_b[j], j > 0);
+                                            max_iter, &it, &est, s, ws, L, true, ev_b[j], j > 0);
             it_max = std::max(it_max, it);
             est_max = std::max(est_max, est);
             if (r != 0 && r != GB_STATUS_NOT_CONVERGED) {

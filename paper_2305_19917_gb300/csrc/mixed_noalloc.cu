@@ -7,18 +7,20 @@
 // driver allocation fails even though its own pool has room), latency- or
 // safety-critical loops that must not call the driver's allocator (it may
 // synchronise the device and may fail at run time), and plug-ins that are
-// only handed buffers.  This entry point takes its work space from a fixed
-// array that is part of the library image instead.
+// only handed buffers.  This entry point takes its work space (and the
+// status word of its bounded waits) from a fixed array that is part of the
+// library image instead, and calls no allocating routine.
 //
 // The scratch array below is a file-scope __device__ object: every GPU that
 // loads the library holds its kNoAllocBytes until the process exits.  Host
 // code cannot use its name as a device address, so the first call on each
 // device (with that device current) looks the address up with
 // cudaGetSymbolAddress and keeps it; make that first call before any stream
-// capture.  All calls share the one array and it keeps the last call's
-// contents: everything that must start at zero is cleared by each call, and
-// calls that overlap on the GPU (on different streams or host threads) race
-// on it -- serialise them.
+// capture.  The kept address belongs to the context that was current then:
+// calls after cudaDeviceReset are not supported.  All calls share the one
+// array and it keeps the last call's contents: everything that must start at
+// zero is cleared by each call, and calls that overlap on the GPU (on
+// different streams or host threads) race on it -- serialise them.
 #include <mutex>
 #include "common.cuh"
 #include "mixed.cuh"
@@ -26,10 +28,9 @@
 namespace gb {
 namespace {
 
-// 16 MiB: a device status word in the first 256 bytes, then the work space
-// of one solve (the same layout as gb_dtrsm_mixed's).
+// 16 MiB: the work space of one solve (the same layout as gb_dtrsm_mixed's,
+// status word included).
 constexpr size_t kNoAllocBytes = size_t(16) << 20;
-constexpr size_t kStatusBytes = 256;
 
 static __device__ __align__(256) unsigned char noalloc_scratch[kNoAllocBytes];
 
@@ -79,18 +80,12 @@ extern "C" int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag, i
         return gb::check(cudaStreamSynchronize(s));
     }
     const gb::MixedLayout L = gb::mixed_layout(side, m, n, prec);
-    if (L.total + gb::kStatusBytes > gb::kNoAllocBytes) return GB_STATUS_SCRATCH_TOO_SMALL;
+    if (L.total > gb::kNoAllocBytes) return GB_STATUS_SCRATCH_TOO_SMALL;
     char *base = nullptr;
     GB_TRY(gb::scratch_address(&base));
-    int *status_word = reinterpret_cast<int *>(base);
-    GB_CUDA(cudaMemsetAsync(status_word, 0, sizeof(int), s));
-    int st = gb::mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, iters_out,
-                            est_err_out, s, base + gb::kStatusBytes, status_word, false, nullptr);
-    if (st == 0 || st == GB_STATUS_NOT_CONVERGED) {
-        int h = 0;
-        const int c = gb::check(cudaMemcpy(&h, status_word, sizeof(int), cudaMemcpyDeviceToHost));
-        if (c) return c;
-        if (h) return GB_STATUS_TIMEOUT;
-    }
-    return st;
+    // no graph (capturing and instantiating one allocates); the solve clears
+    // and reads its status word itself and returns GB_STATUS_TIMEOUT with B
+    // unchanged if a bounded wait gave up
+    return gb::mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, iters_out,
+                          est_err_out, s, base, false, nullptr);
 }

@@ -181,12 +181,10 @@ size_t bwd_smem(int D) { return sizeof(float) * size_t(pcount(D) + S * D + 3 * S
 
 int set_attrs(int D)
 {
-    static int done_for = -1;
-    if (done_for != D) {
-        GB_CUDA(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(D)));
-        GB_CUDA(cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(D)));
-        done_for = D;
-    }
+    // the limit depends on the input width D: set per call (cheap next to
+    // the kernels, and correct on whichever device is current)
+    GB_CUDA(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(D)));
+    GB_CUDA(cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(D)));
     return 0;
 }
 

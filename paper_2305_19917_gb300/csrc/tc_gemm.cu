@@ -383,28 +383,17 @@ tc_gemm_bf16_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __
 template <int BN>
 static int prepare_bn()
 {
-    static bool attr = false;
-    if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(tc_gemm_bf16_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TileCfg<BN>::SMEM_BYTES));
-        attr = true;
-    }
-    return 0;
+    static PerDeviceOnce attr;
+    return smem_attr_once(attr, tc_gemm_bf16_kernel<BN>, TileCfg<BN>::SMEM_BYTES);
 }
 
-// One-time per-process set-up (kernel attributes, device status word); must
-// run before any stream capture that launches the kernel.
+// One-time per-device set-up (kernel attributes); must run before any
+// stream capture that launches the kernel.
 template <int PBN>
 static int prepare_persistent()
 {
-    static bool attr = false;
-    if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(tc_gemm_bf16_persistent_kernel<PBN>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)PCfg<PBN>::smem_for(PCfg<PBN>::STAGES)));
-        attr = true;
-    }
-    return 0;
+    static PerDeviceOnce attr;
+    return smem_attr_once(attr, tc_gemm_bf16_persistent_kernel<PBN>, PCfg<PBN>::smem_for(PCfg<PBN>::STAGES));
 }
 
 static int num_sms()
@@ -422,8 +411,7 @@ int tc_gemm_prepare()
     GB_TRY(prepare_persistent<128>());
     GB_TRY(prepare_persistent<64>());
     if (num_sms() <= 0) return GB_STATUS_CUDA_ERROR;
-    GB_TRY(prepare_bn<64>());
-    return device_status_word() ? 0 : GB_STATUS_CUDA_ERROR;
+    return prepare_bn<64>();
 }
 
 template <int BN>

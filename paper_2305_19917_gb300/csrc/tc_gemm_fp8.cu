@@ -157,13 +157,8 @@ tc_gemm_fp8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
 int tc_gemm_fp8_prepare()
 {
-    static bool attr = false;
-    if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(tc_gemm_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES));
-        attr = true;
-    }
-    return 0;
+    static PerDeviceOnce attr;
+    return smem_attr_once(attr, tc_gemm_fp8_kernel, SMEM_BYTES);
 }
 
 // C (M x N FP32 column-major) = alpha*C - A8*B8 with the block scales above;

@@ -21,21 +21,15 @@
 // pipe of an SM retires two operations per clock: done here, that work
 // would idle the tensor cores of the SM for tens of microseconds per tile.
 //
-// One CTA per 128 x 128 tile of R; the CTAs run in clusters of two that
-// hold vertically adjacent row tiles of the same columns, so both need the
-// same correction digits: each CTA loads one 64-column half of every Z tile
-// and multicasts it to both (L2 reads per CTA and K step: 16 KB of A plus
-// 16 or 8 KB of Z instead of 16 + 32).  Pass p multiplies slice a_p
-// (128 x 64 per stage) with [z_1; z_2] (256 x 64, both slices of the same
-// 128 columns; z_2 only in passes p < P2) into one of two 128 x 256 TMEM
-// accumulators, so that draining pass p overlaps the MMAs of pass p+1.
-// Both CTAs of a pair step through the same K range (the longer of the
-// two); the upper tile issues no MMAs for the K steps above its diagonal.
-// A stage is refilled only after both CTAs' MMAs released it (each MMA
-// commit arrives on the stage's empty barrier in both CTAs).  Warp 0: TMA,
-// warp 1: TMEM + MMA issue, warps 2-9: epilogue (warp w drains TMEM lanes
-// 32*(w%4).., column half (w-2)/4).  Pairs are rasterised in groups of 4
-// (8 row tiles).
+// One CTA per 128 x 128 tile of R, with no cluster: each CTA loads its own
+// A slice tile (128 x 64 per stage) and both correction slices of its 128
+// columns (two 128 x 64 tiles), so no load is shared between CTAs (L2 reads
+// per CTA and K step: 16 KB of A plus 32 or 16 KB of Z).  Pass p multiplies
+// slice a_p with [z_1; z_2] (256 x 64, z_2 only in passes p < P2) into one of
+// two 128 x 256 TMEM accumulators, so that draining pass p overlaps the MMAs
+// of pass p+1.  Warp 0: TMA, warp 1: TMEM + MMA issue, warps 2-9: epilogue
+// (warp w drains TMEM lanes 32*(w%4).., column half (w-2)/4).  Tiles are
+// rasterised in groups of 8 row tiles, longest K ranges (lowest rows) first.
 #include "common.cuh"
 #include "tc_common.cuh"
 
@@ -53,12 +47,12 @@ constexpr uint32_t B_BYTES = 2 * ZS_BYTES;         // z_1 and z_2 tiles
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr size_t SMEM_BYTES = 1024 + STAGES * size_t(STAGE_BYTES) + 256;
 constexpr int NTHREADS = 320;
-constexpr uint16_t kPair = 0x3;
+constexpr int kRasterGroup = 8;
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS, 1)
 tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ,
-                   long long *__restrict__ Tg, int64_t ldr, int k_lo,
-                   int k_hi, int P, int P2, int W, int nMt, int nMp, int nNt, int *status)
+                   long long *__restrict__ Tg, int64_t ldr, int k_lo, int k_hi, int P, int P2, int W, int nMt,
+                   int nNt, int *status)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -72,18 +66,13 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rank = int(tc::cluster_ctarank());
-    int pg, n_blk;
-    tc::raster_grouped(int(blockIdx.x >> 1), nMp, nNt, 4, pg, n_blk);
-    // longest K ranges first; rank 0 holds the lower tile of the pair, rank
-    // 1 the one above it (absent when nMt is odd and this is the top pair)
-    const int m0 = nMt - 1 - 2 * pg;
-    const int m_blk = m0 - rank;
-    const bool ghost = m_blk < 0;
-    const int i0 = ghost ? 0 : m_blk * BM, j0 = n_blk * BNO;
-    const int k_end = min(k_hi, m0 * BM + BM);                 // the pair's K range
-    const int k_own = ghost ? k_lo : min(k_hi, i0 + BM);       // this tile's
-    if (k_end <= k_lo) return;  // both tiles entirely above the diagonal
+    int gm, n_blk;
+    tc::raster_grouped(int(blockIdx.x), nMt, nNt, kRasterGroup, gm, n_blk);
+    // longest K ranges first: the lowest row tiles are rasterised first
+    const int m_blk = nMt - 1 - gm;
+    const int i0 = m_blk * BM, j0 = n_blk * BNO;
+    const int k_end = min(k_hi, i0 + BM);  // this tile's K range is [k_lo, k_end)
+    if (k_end <= k_lo) return;             // the tile lies entirely above the diagonal
     // exactness needs K <= 1024 per tensor-memory accumulation: the K range
     // is cut into chunks of at most 1024, each pass of each chunk drained
     // separately into the same int64 sums
@@ -94,7 +83,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
             tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 2);  // one MMA commit from each CTA of the pair
+            tc::mbar_init(&empty[s], 1);  // one MMA commit
         }
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&accf[b], 1);
@@ -105,8 +94,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     }
     if (warp == 1) tc::tmem_alloc(tslot, 512);
     tc::tc_fence_before();
-    // the peer may multicast into this CTA only after its barriers exist
-    tc::cluster_sync();
+    __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
     volatile int *ab = &abort_flag;
@@ -128,16 +116,14 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         ok = false;
                         break;
                     }
-                    const bool own = kk < k_own;
-                    tc::mbar_arrive_expect_tx(&full[s], (own ? A_BYTES : 0u) + uint32_t(nsl) * ZS_BYTES);
-                    if (own) tc::tma_load_3d(&tmA, &full[s], sA + s * A_BYTES, kk, i0, p);
+                    tc::mbar_arrive_expect_tx(&full[s], A_BYTES + uint32_t(nsl) * ZS_BYTES);
+                    tc::tma_load_3d(&tmA, &full[s], sA + s * A_BYTES, kk, i0, p);
                     for (int q = 0; q < nsl; q++)
-                        tc::tma_load_3d_mc(&tmZ, &full[s], sB + s * B_BYTES + q * ZS_BYTES + rank * (ZS_BYTES / 2),
-                                           kk, j0 + rank * (BNO / 2), q, kPair);
+                        tc::tma_load_3d(&tmZ, &full[s], sB + s * B_BYTES + q * ZS_BYTES, kk, j0, q);
                 }
             }
-            // tail: wait until both CTAs released every stage, so that no
-            // commit of the peer is still on its way to this CTA's barriers
+            // tail: wait until the MMAs released every stage, so that no
+            // commit is still on its way to this CTA's barriers when it exits
             for (int t = 0; t < STAGES && ok; t++, g++) {
                 const int s = g % STAGES;
                 const uint32_t ph = (g / STAGES) & 1;
@@ -167,15 +153,13 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         break;
                     }
                     tc::tc_fence_after();
-                    if (kc0 + kt * BK < k_own) {  // this tile's K steps are a prefix of the chunk
-                        const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
-                        const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
+                    const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
+                    const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
 #pragma unroll
-                        for (int kk = 0; kk < BK / 16; kk++)
-                            tc::mma_f16(d, tc::desc_kmajor_sw128(a0 + kk * 32),
-                                        tc::desc_kmajor_sw128(b0 + kk * 32), idesc, (kt | kk) != 0);
-                    }
-                    tc::mma_commit_mc(&empty[s], kPair);
+                    for (int kk = 0; kk < BK / 16; kk++)
+                        tc::mma_f16(d, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
+                                    idesc, (kt | kk) != 0);
+                    tc::mma_commit(&empty[s]);
                 }
                 tc::mma_commit(&accf[buf]);
                 if (!ok) break;
@@ -190,7 +174,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         for (int c = 0; c < 64; c++) T[c] = 0;
         bool ok = true;
         for (int cp = 0; cp < npass; cp++) {
-            const int c = cp / P, p = cp % P;
+            const int p = cp % P;
             const int buf = cp & 1;
             const uint32_t use = cp >> 1;
             if (!tc::mbar_wait(&accf[buf], use & 1, ab, status, tc::TC_TIMEOUT_EPILOGUE)) {
@@ -198,35 +182,32 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 break;
             }
             tc::tc_fence_after();
-            // a chunk that starts at or above this tile's diagonal received no MMA
-            if (k_lo + c * KC < k_own) {
-                const bool two = p < P2;
-                const int s1 = W - (8 * (p + 1) + 8);
-                const int s2 = W - (8 * (p + 1) + 16);
-                const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 256 + half * 64);
+            const bool two = p < P2;
+            const int s1 = W - (8 * (p + 1) + 8);
+            const int s2 = W - (8 * (p + 1) + 16);
+            const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 256 + half * 64);
 #pragma unroll
-                for (int c0 = 0; c0 < 64; c0 += 16) {
-                    uint32_t r1[16];
-                    tc::tmem_ld16(tbase + c0, r1);
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                uint32_t r1[16];
+                tc::tmem_ld16(tbase + c0, r1);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 16; j++)
+                    T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r1[j]))) << s1;
+                if (two) {
+                    uint32_t r2[16];
+                    tc::tmem_ld16(tbase + 128 + c0, r2);
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 16; j++)
-                        T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r1[j]))) << s1;
-                    if (two) {
-                        uint32_t r2[16];
-                        tc::tmem_ld16(tbase + 128 + c0, r2);
-                        tc::tmem_ld_wait();
-#pragma unroll
-                        for (int j = 0; j < 16; j++)
-                            T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r2[j]))) << s2;
-                    }
+                        T[c0 + j] += static_cast<long long>(__float2int_rn(__uint_as_float(r2[j]))) << s2;
                 }
             }
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acce[buf]);
         }
-        if (ok && !ghost) {
+        if (ok) {
             // the exact sums of this tile: lanes hold consecutive rows, so
             // each store instruction writes 256 contiguous bytes
             const int64_t o = i0 + row + int64_t(j0 + half * 64) * ldr;
@@ -236,8 +217,6 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     }
     tc::tc_fence_before();
     __syncthreads();
-    // neither CTA leaves while the other may still write into its shared memory
-    tc::cluster_sync();
     if (warp == 1) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, 512);
@@ -278,21 +257,17 @@ int launch_tc_residual(long long *Tg, int64_t ldr, const void *As, const void *Z
     {
         uint64_t dims[3] = {uint64_t(kp), uint64_t(np), 2};
         uint64_t strides[2] = {uint64_t(kp) * 2, uint64_t(np) * uint64_t(kp) * 2};
-        uint32_t box[3] = {BK, BNO / 2, 1};  // one column half of one slice
+        uint32_t box[3] = {BK, BNO, 1};  // 128 columns of one slice
         GB_TRY(encode_tmap(&tz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Zs, dims, strides, box));
     }
-    static bool attr = false;
-    if (!attr) {
-        GB_CUDA(cudaFuncSetAttribute(tc_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES));
-        attr = true;
-    }
+    static PerDeviceOnce attr;
+    GB_TRY(smem_attr_once(attr, tc_residual_kernel, SMEM_BYTES));
     int *st = status ? status : device_status_word();
     if (!st) return GB_STATUS_CUDA_ERROR;
-    // 1-D grid of clusters of 2 over (row-tile pairs) x (column tiles)
-    const int64_t nM = kp / BM, nN = np / BNO, nMp = (nM + 1) / 2;
-    if (nM > 65535 || nN > 65535 || 2 * nMp * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
-    dim3 grid((unsigned)(2 * nMp * nN));
+    // 1-D grid over (row tiles) x (column tiles)
+    const int64_t nM = kp / BM, nN = np / BNO;
+    if (nM > 65535 || nN > 65535 || nM * nN > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
+    dim3 grid((unsigned)(nM * nN));
     // algorithmic work: P passes (P2 of them two slices wide) over the lower
     // triangle of the K range
     double tri = 0;
@@ -303,9 +278,8 @@ int launch_tc_residual(long long *Tg, int64_t ldr, const void *As, const void *Z
     double flops = 0;
     for (int p = 0; p < P; p++) flops += 2.0 * BM * tri * np * (p < P2 ? 2 : 1);
     LaunchScope ls(KK_RESIDUAL, s, flops, 8.0 * kp * np);
-    tc_residual_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(
-        ta, tz, Tg, ldr, (int)k_lo,
-        (int)k_hi, P, P2, W, (int)nM, (int)nMp, (int)nN, st);
+    tc_residual_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ta, tz, Tg, ldr, (int)k_lo, (int)k_hi, P, P2, W,
+                                                          (int)nM, (int)nN, st);
     return check(cudaGetLastError());
 }
 
