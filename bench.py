@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--prec", default="bf16", choices=["bf16", "fp8"], help="mixed path low precision")
     p.add_argument("--count", type=int, default=4096, help="batched path: number of problems")
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison leg")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the other configurations (FP8 mixed, 32768 x 4096, the 16 plain FP64 forms)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-cols", type=int, default=0,
                    help="right-hand sides in the oracle sample (0 = auto, ~10-30 s)")
@@ -222,6 +224,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     from paper_2305_19917_gb300 import api, inputs
+    from paper_2305_19917_gb300 import dist as gdist
 
     rank, world, local = dist_env()
     if world > 1:
@@ -236,8 +239,13 @@ def run_ours(args):
     tol, max_iter = 1e-11, 60
     prec = api.PREC_FP8 if args.prec == "fp8" else api.PREC_BF16
 
-    # Host inputs (seeded), device copies.
+    # One problem with world * n right-hand sides, sharded over the ranks
+    # (n per GPU, no exchange): every rank holds A and its own block of B.
+    # Host inputs (seeded; rank 0's block is the single-GPU workload's B),
+    # device copies.
     A_h, B_h = inputs.make_problem(side, uplo, trans, diag, m, n, seed=0)
+    if rank > 0:
+        B_h = np.asfortranarray(np.random.default_rng(10_000 + rank).standard_normal((m, n)))
     A = api.to_device_colmajor(A_h, torch.float64)
     B0 = api.to_device_colmajor(B_h, torch.float64)
     B = api.colmajor_empty(m, n, torch.float64)
@@ -249,12 +257,16 @@ def run_ours(args):
         B.copy_(B0)
 
     def solve_mixed():
-        st, it, est = api.trsm_mixed(side, uplo, trans, diag, alpha, A, B, tol=tol, prec=prec, max_iter=max_iter,
-                                     stream=stream)
+        _, _, st, it, est = gdist.solve_sharded(side, uplo, trans, diag, alpha, A, B, rank=rank, world=world,
+                                                total=world * n, path="mixed", tol=tol, prec=prec,
+                                                max_iter=max_iter, stream=stream)
+        if st < 0 or st in (api.STATUS_CUDA_ERROR, api.STATUS_TIMEOUT):
+            raise api.GbError("gb_dtrsm_mixed", st)
         return st, it, est, api.gb_mixed_history()
 
     def solve_fp64():
-        api.trsm(side, uplo, trans, diag, alpha, A, B, stream=stream)
+        gdist.solve_sharded(side, uplo, trans, diag, alpha, A, B, rank=rank, world=world, total=world * n,
+                            path="plain", stream=stream)
         return None
 
     solve = solve_mixed if mixed else solve_fp64
@@ -323,7 +335,7 @@ def run_ours(args):
             B_pin.copy_(B_host0)
             api.trsm_mixed_host(side, uplo, trans, diag, alpha, A_pin, B_pin, tol=tol, prec=prec,
                                 max_iter=max_iter, stream=stream)
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 6))):
         B_pin.copy_(B_host0)  # fresh right-hand sides (host copy, not timed)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -381,6 +393,13 @@ def run_ours(args):
                 "launches": p["launches"], "ms_total": p["ms"],
                 "share": p["ms"] / max(1e-9, sum(v["ms"] for v in prof.values()))}
 
+    extras = None
+    if mixed and not args.no_extras:
+        # free the headline workload's buffers first (the extras need up to ~20 GB)
+        del A, B0, B
+        torch.cuda.empty_cache()
+        extras = run_extras(stream, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cols = args.cpu_sample_cols or auto_sample_cols(m)[0]
@@ -399,13 +418,17 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": (args.prec + "+f64") if mixed else "f64", "data": "synthetic",
                 "config": {"workload": wl, "global_batch": world,
+                           "sharding": (f"one problem with {world} x {n} right-hand sides split over {world} "
+                                        f"GPU(s), {n} per GPU (columns of B; no collective on the data path)"),
                            "l2": "inputs larger than L2 (4 GiB); B re-copied before each step"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": world * flops / (e2e_t * 1e-3) / 1e12, "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "ms_per_step": [round(float(x), 3) for x in e2e_ms]},
+                        "ms_per_step": [round(float(x), 3) for x in e2e_ms],
+                        "ms_mean": e2e_t, "ms_median": float(np.median(e2e_ms)),
+                        "value_at_median": world * flops / (float(np.median(e2e_ms)) * 1e-3) / 1e12},
                 "gpu_launches": int(launches), "clocks": clk, "accuracy": acc,
-                "plain_fp64": plain, "wall_s_timed": wall,
+                "plain_fp64": plain, "wall_s_timed": wall, "other_configs": extras,
                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
                                 "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 else 0.0)}
                             for k, v in prof.items() if v["launches"]}}
@@ -415,11 +438,111 @@ def run_ours(args):
     return 0
 
 
+def _time_calls(fn, reset, steps, warm, stream):
+    import torch
+    for _ in range(warm):
+        reset()
+        fn()
+    torch.cuda.synchronize()
+    ms, outs = _timed_steps(fn, reset, steps, stream)
+    return float(np.mean(ms)), outs
+
+
+def run_extras(stream, rank):
+    """The other configurations, timed briefly on the same GPU (device-
+    resident inputs, CUDA events, B reset outside the events):
+      * mixed FP8 E4M3 (per-block power-of-two scales) at m = n = 16384;
+      * mixed BF16 and FP8 at m = 32768, n = 4096, with plain FP64 beside them;
+      * plain FP64 at m = n = 8192 in all 16 side/uplo/trans/diag forms and at
+        m = n = 16384 in two more forms (Right/Upper/T/Unit, Left/Upper/T/NonUnit),
+        alpha = 1.5.
+    Inputs come from the seeded device generator (same distributions as the
+    headline's); accuracy is checked on sampled columns (rows for side Right)
+    against the CPU oracle."""
+    import torch
+
+    import oracle
+    from paper_2305_19917_gb300 import api, inputs
+
+    out = {}
+    alpha, tol = 1.5, 1e-11
+
+    def sampled_err(side, uplo, trans, diag, A, B_orig, X):
+        m, n = X.shape
+        if side == 0:
+            idx = [0, n // 2, n - 1]
+            Bs, Xs = B_orig[:, idx], X[:, idx]
+        else:
+            idx = [0, m // 2, m - 1]
+            Bs, Xs = B_orig[idx, :], X[idx, :]
+        Ah = A.cpu().numpy()
+        Xo = oracle.dtrsm(side, uplo, trans, diag, alpha, Ah, Bs.cpu().numpy())
+        return float(np.linalg.norm(Xs.cpu().numpy() - Xo) / np.linalg.norm(Xo))
+
+    def mixed_leg(name, A, B0, prec, seed_note):
+        m, n = B0.shape
+        B = api.colmajor_empty(m, n, torch.float64)
+        reset = lambda: B.copy_(B0)  # noqa: E731
+        p = api.PREC_FP8 if prec == "fp8" else api.PREC_BF16
+        fn = lambda: api.trsm_mixed(0, 0, 0, 0, alpha, A, B, tol=tol, prec=p, max_iter=60,  # noqa: E731
+                                    stream=stream)
+        t, outs = _time_calls(fn, reset, 2, 1, stream)
+        err = sampled_err(0, 0, 0, 0, A, B0, B) if rank == 0 else None
+        out[name] = {"workload": f"mixed {prec.upper()} + refinement Left/Lower/N/NonUnit m={m} n={n}, "
+                                 f"alpha=1.5, tol 1e-11, {seed_note}",
+                     "ms_per_step": t, "tflops": float(m) * m * n / (t * 1e-3) / 1e12,
+                     "refinement_steps": outs[-1][1], "status": outs[-1][0], "est_err": outs[-1][2],
+                     "history_rho_levels": api.gb_mixed_history(), "fwd_err_sampled": err}
+        del B
+
+    def plain_leg(name, side, uplo, trans, diag, A, B0, steps=1):
+        m, n = B0.shape
+        B = api.colmajor_empty(m, n, torch.float64)
+        reset = lambda: B.copy_(B0)  # noqa: E731
+        fn = lambda: api.trsm(side, uplo, trans, diag, alpha, A, B, stream=stream)  # noqa: E731
+        t, _ = _time_calls(fn, reset, steps, 1, stream)
+        err = sampled_err(side, uplo, trans, diag, A, B0, B) if rank == 0 else None
+        fl = float(m) * m * n if side == 0 else float(m) * n * n
+        out[name] = {"workload": f"plain FP64 side={side} uplo={uplo} trans={trans} diag={diag} m={m} n={n}, "
+                                 f"alpha=1.5, planner default plan",
+                     "ms_per_step": t, "tflops": fl / (t * 1e-3) / 1e12, "fwd_err_sampled": err}
+        del B
+
+    # mixed FP8 at 16384^2 (BF16 is the headline)
+    A, B0 = inputs.make_problem_device(0, 0, 0, 0, 16384, 16384, seed=0)
+    mixed_leg("mixed_fp8_16384", A, B0, "fp8", "device generator seed 0")
+    del A, B0
+    # 32768 x 4096: BF16, FP8 and plain FP64
+    A, B0 = inputs.make_problem_device(0, 0, 0, 0, 32768, 4096, seed=1)
+    mixed_leg("mixed_bf16_32768x4096", A, B0, "bf16", "device generator seed 1")
+    mixed_leg("mixed_fp8_32768x4096", A, B0, "fp8", "device generator seed 1")
+    plain_leg("plain_fp64_32768x4096", 0, 0, 0, 0, A, B0)
+    for nm in ("mixed_bf16_32768x4096", "mixed_fp8_32768x4096"):
+        out[nm]["speedup_vs_plain_fp64"] = out["plain_fp64_32768x4096"]["ms_per_step"] / out[nm]["ms_per_step"]
+    del A, B0
+    torch.cuda.empty_cache()
+    # plain FP64, all 16 forms at 8192^2
+    for uplo in (0, 1):
+        A, B0 = inputs.make_problem_device(0, uplo, 0, 0, 8192, 8192, seed=2 + uplo)
+        for side in (0, 1):
+            for trans in (0, 1):
+                for diag in (0, 1):
+                    plain_leg(f"plain_fp64_8192_s{side}u{uplo}t{trans}d{diag}", side, uplo, trans, diag, A, B0)
+        del A, B0
+    # two more forms at 16384^2
+    A, B0 = inputs.make_problem_device(1, 1, 1, 1, 16384, 16384, seed=4)
+    plain_leg("plain_fp64_16384_s1u1t1d1", 1, 1, 1, 1, A, B0)
+    plain_leg("plain_fp64_16384_s0u1t1d0", 0, 1, 1, 0, A, B0)
+    del A, B0
+    torch.cuda.empty_cache()
+    return out
+
+
 # DRAM bytes (read + write) per launch of the residual kernel, from one ncu
 # capture of the full-size workload (dram__bytes_read.sum + dram__bytes_write.sum,
 # mean of the two launches of one solve).  Only valid for the kernel as it was
 # when captured; drop the entry when the kernel changes.
-RESIDUAL_DRAM_BYTES = {(16384, 16384, "bf16"): 19.17e9}
+RESIDUAL_DRAM_BYTES = {}
 
 # FP32 ALU peak for the batched FP32 roofline: 152 SMs x 128 FFMA/clk x 2
 # flop x 2.07 GHz (an FFMA probe measured 69.8 TFLOP/s).

@@ -146,12 +146,18 @@ enum { GB_PREC_BF16 = 0, GB_PREC_FP8 = 1 };
  * solution must stay within the FP32 range of that solve (about 3.4e38 times
  * the column's largest |alpha*B|): beyond it, or with non-finite data, the
  * call returns GB_STATUS_RANGE with B unchanged.
+ * The kernels' bounded device waits record a timeout in a status word of
+ * the call's own work space, read back at every refinement step: a wait
+ * that gave up returns GB_STATUS_TIMEOUT with B unchanged.
  * Synchronous: returns after the solve is complete.  Work space (about
- * 14 k^2 + 42 k n bytes, k and n rounded up to multiples of 128) comes from a
- * library-owned stream-ordered pool.  The low-precision solve is replayed
+ * 14 k^2 + 42 k n bytes, k and n rounded up to multiples of 128) is a
+ * library-owned buffer per device, taken from a stream-ordered pool on first
+ * use, kept between calls (so that its address, and the graphs below that
+ * name it, stay valid) and regrown when a larger problem needs it;
+ * gb_mixed_workspace_release frees it.  The low-precision solve is replayed
  * from a CUDA graph cached per device (the 4 most recently used problem
  * shapes and work spaces); calls on one device from several host threads are
- * serialised while they use it.
+ * serialised.
  */
 int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
                    int64_t n, double alpha, const double *A, int64_t lda,
@@ -161,18 +167,20 @@ int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
 /*
  * gb_dtrsm_mixed_noalloc: gb_dtrsm_mixed for callers that cannot allocate
  * device memory (the paper has no counterpart; this is an interface
- * addition).  Same arguments, results and status codes as gb_dtrsm_mixed;
- * it calls no allocator: its work space is a fixed 16 MiB array inside the
- * library image (held on every GPU that loads the library until the process
- * exits).  That bounds the problem: the padded sizes kp = 128*ceil(k/128),
+ * addition).  Same arguments, results and status codes as gb_dtrsm_mixed
+ * (GB_STATUS_TIMEOUT included), plus GB_STATUS_SCRATCH_TOO_SMALL; it calls
+ * no allocator: its work space and status word are a fixed 16 MiB array
+ * inside the library image (held on every GPU that loads the library until
+ * the process exits).  That bounds the problem: the padded sizes kp = 128*ceil(k/128),
  * np = 128*ceil(ncols/128) (k = order of A, ncols = right-hand sides) must
  * satisfy roughly 14 kp^2 + 42 kp np + 1550 kp + 20 np + 4 KB <= 16 MiB
  * (e.g. k = ncols = 512); larger problems return GB_STATUS_SCRATCH_TOO_SMALL
  * without touching the GPU.  The first call on a device performs a one-time
- * set-up (it looks up the array's device address), so make it before any
- * stream capture.  Calls share the array: calls that overlap on the GPU race
- * and must be serialised by the caller.  Synchronous, like gb_dtrsm_mixed;
- * a device wait that timed out returns GB_STATUS_TIMEOUT.
+ * set-up (it looks up the array's device address and keeps it), so make it
+ * before any stream capture; the kept address belongs to that context, so
+ * calls after cudaDeviceReset are not supported.  Calls share the array:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * Synchronous, like gb_dtrsm_mixed.
  */
 int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag,
                            int64_t m, int64_t n, double alpha,
@@ -194,8 +202,9 @@ int gb_dtrsm_mixed_noalloc(int side, int uplo, int trans, int diag,
  * block's refinement stops on its own criterion; iters_out and est_err_out
  * report the largest over the blocks.  On an error in a later block the
  * columns already copied back are restored: B is unchanged, as for
- * gb_dtrsm_mixed.  Device buffers come from the library's memory pool and
- * are released before it returns.  For the copies to overlap with
+ * gb_dtrsm_mixed.  Device buffers (work space, A, B and the X blocks) are
+ * the library's cached per-device work space of gb_dtrsm_mixed, grown to
+ * fit.  For the copies to overlap with
  * computation, A and B should be page-locked (cudaHostAlloc or
  * cudaHostRegister); pageable memory gives the same result, slower.
  * alpha == 0 sets B = 0 on the host without reading A.  Synchronous.
@@ -213,6 +222,15 @@ int gb_dtrsm_mixed_host(int side, int uplo, int trans, int diag,
  * and sizes.  Host-only; -1 for negative sizes.
  */
 int64_t gb_mixed_host_bytes(int side, int uplo, int64_t m, int64_t n, int64_t *d2h_bytes);
+
+/*
+ * gb_mixed_workspace_release: frees the cached work space of gb_dtrsm_mixed
+ * and gb_dtrsm_mixed_host on the current device, after `stream` is idle (the
+ * next call allocates it again; the cached graphs that name it are then not
+ * replayed unless the new buffer lands at the same address with the same
+ * layout).  Returns 0 or GB_STATUS_CUDA_ERROR.
+ */
+int gb_mixed_workspace_release(void *stream);
 
 /*
  * gb_mixed_history: refinement history of the last gb_dtrsm_mixed call made

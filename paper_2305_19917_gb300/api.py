@@ -57,6 +57,7 @@ _SIGS = {
     "gb_dtrsm_mixed_host": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32,
                              ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
     "gb_mixed_host_bytes": ([i32, i32, i64, i64, ctypes.POINTER(i64)], i64),
+    "gb_mixed_workspace_release": ([vp], i32),
     "gb_trsm_batched": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "gb_batched_plan_create": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                 ctypes.POINTER(vp)], i32),
@@ -177,6 +178,11 @@ def gb_mixed_host_bytes(side, uplo, m, n):
     d2h = i64()
     h2d = lib().gb_mixed_host_bytes(side, uplo, m, n, ctypes.byref(d2h))
     return int(h2d), int(d2h.value)
+
+
+def gb_mixed_workspace_release(stream=0):
+    """Free the mixed solves' cached work space on the current device."""
+    return lib().gb_mixed_workspace_release(stream or None)
 
 
 class _BatchArgs:

@@ -1011,15 +1011,78 @@ struct LowGraph {
 };
 constexpr int kGraphs = 4;
 
-// Solves that replay cached graphs on one device are serialised: a graph in
-// use must not be evicted (destroyed) by another host thread's solve.
-std::mutex &graph_mutex()
+}  // namespace
+
+// Solves that replay cached graphs or use the cached work space on one
+// device are serialised: a graph in use must not be evicted (destroyed), nor
+// the work space regrown, by another host thread's solve.  Recursive, so that
+// an entry point can hold it around the whole call.
+std::recursive_mutex &mixed_device_mutex()
 {
-    static std::mutex mu[64];
+    static std::recursive_mutex mu[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
     return mu[dev];
 }
+
+// The allocating entry points' work space: one buffer per device from the
+// library's pool, kept between calls and regrown when a larger problem needs
+// more (the old buffer is released once the stream is idle).  A stable
+// address means the captured low-precision graphs, which name the work
+// space's buffers, are found again on the next call instead of being
+// captured anew.  The caller holds mixed_device_mutex().
+struct DeviceWorkspace {
+    char *base = nullptr;
+    size_t size = 0;
+};
+static DeviceWorkspace g_ws[64];
+
+int mixed_workspace(size_t bytes, cudaStream_t s, char **out)
+{
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GB_STATUS_CUDA_ERROR;
+    DeviceWorkspace &w = g_ws[dev];
+    if (w.size < bytes) {
+        cudaMemPool_t pool = library_pool();
+        if (!pool) return GB_STATUS_CUDA_ERROR;
+        if (w.base) {
+            GB_CUDA(cudaStreamSynchronize(s));
+            GB_CUDA(cudaFreeAsync(w.base, s));
+            w.base = nullptr;
+            w.size = 0;
+        }
+        // some headroom, so that slightly larger problems do not regrow it
+        const size_t want = bytes + bytes / 16;
+        char *p = nullptr;
+        GB_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&p), want, pool, s));
+        w.base = p;
+        w.size = want;
+    }
+    *out = w.base;
+    return 0;
+}
+
+}  // namespace gb
+
+extern "C" int gb_mixed_workspace_release(void *stream)
+{
+    std::lock_guard<std::recursive_mutex> lk(gb::mixed_device_mutex());
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GB_STATUS_CUDA_ERROR;
+    gb::DeviceWorkspace &w = gb::g_ws[dev];
+    if (!w.base) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GB_CUDA(cudaStreamSynchronize(s));
+    GB_CUDA(cudaFreeAsync(w.base, s));
+    w.base = nullptr;
+    w.size = 0;
+    return gb::check(cudaStreamSynchronize(s));
+}
+
+namespace gb {
+namespace {
 
 int low_graph(LowExec &le, const void *ws, LowGraph **out)
 {
@@ -1239,7 +1302,7 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
     const int hist0 = merge_hist ? tl_nhist : 0;
     int hist = 0;
     if (!merge_hist) tl_nhist = 0;
-    std::unique_lock<std::mutex> graph_lock(graph_mutex(), std::defer_lock);
+    std::unique_lock<std::recursive_mutex> graph_lock(mixed_device_mutex(), std::defer_lock);
 
     int st = 0;
     // the norms of a step and the status word, read back together
@@ -1404,14 +1467,11 @@ int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t
                      double *est_err_out, cudaStream_t s)
 {
     const MixedLayout L = mixed_layout(side, m, n, prec);
-    cudaMemPool_t pool = library_pool();
-    if (!pool) return GB_STATUS_CUDA_ERROR;
+    std::lock_guard<std::recursive_mutex> lk(mixed_device_mutex());
     char *ws = nullptr;
-    GB_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&ws), L.total, pool, s));
-    const int st = mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter,
-                              iters_out, est_err_out, s, ws, true, nullptr);
-    cudaFreeAsync(ws, s);
-    return st;
+    GB_TRY(mixed_workspace(L.total, s, &ws));
+    return mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, iters_out,
+                      est_err_out, s, ws, true, nullptr);
 }
 
 }  // namespace gb

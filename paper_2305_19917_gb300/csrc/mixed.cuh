@@ -1,6 +1,7 @@
 // Mixed-precision solve: work-space layout and core routine shared by the
 // allocating entry point and the no-allocation one (internal header).
 #pragma once
+#include <mutex>
 #include <stddef.h>
 #include <stdint.h>
 #include <cuda_runtime.h>
@@ -46,6 +47,13 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
                   cudaEvent_t b_ready, bool merge_hist);
 // The library's stream-ordered memory pool for work space (current device).
 cudaMemPool_t mixed_pool();
+// Per-device lock of the mixed solves that use cached graphs or the cached
+// work space (recursive: held by an entry point around its whole call).
+std::recursive_mutex &mixed_device_mutex();
+// The cached work space of the current device, at least `bytes` long
+// (allocated or regrown from the library's pool on stream s); the caller
+// holds mixed_device_mutex() while it uses it.
+int mixed_workspace(size_t bytes, cudaStream_t s, char **out);
 
 // Argument checks of gb_dtrsm_mixed (0 or -i).
 int mixed_validate(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,

@@ -15,8 +15,8 @@
 // j + 1 is solved.  X of every block but the last goes to a separate device
 // buffer, so B's original values stay on the device until the end: when a
 // later block fails (e.g. GB_STATUS_RANGE), the columns already copied back
-// are restored and B is left as it was.  Device memory comes from the
-// library's pool.  The transfers overlap computation only when the host
+// are restored and B is left as it was.  Device memory is the library's
+// cached per-device work space (see gb_mixed_workspace_release).  The transfers overlap computation only when the host
 // buffers are page-locked (cudaHostAlloc / cudaHostRegister); with pageable
 // buffers the result is the same, the copies are just not overlapped.
 #include <algorithm>
@@ -129,8 +129,6 @@ extern "C" int gb_dtrsm_mixed_host(int side, int uplo, int trans, int diag, int6
     int64_t cw = (ncols + nb_req - 1) / nb_req;
     cw = std::min<int64_t>(ncols, (cw + 127) / 128 * 128);
     const int nblk = int((ncols + cw - 1) / cw);
-    cudaMemPool_t pool = gb::mixed_pool();
-    if (!pool) return GB_STATUS_CUDA_ERROR;
     const gb::MixedLayout L = left ? gb::mixed_layout(side, m, cw, prec) : gb::mixed_layout(side, cw, n, prec);
     // device: work space | A | B | X of the blocks before the last
     const int64_t xcols = int64_t(nblk - 1) * cw;
@@ -139,8 +137,11 @@ extern "C" int gb_dtrsm_mixed_host(int side, int uplo, int trans, int diag, int6
     const size_t x_bytes = size_t(k) * size_t(xcols) * 8;
     const size_t a_off = (L.total + 255) / 256 * 256, b_off = a_off + (a_bytes + 255) / 256 * 256;
     const size_t x_off = b_off + (b_bytes + 255) / 256 * 256;
+    // the device's cached work space (kept between calls, so that the
+    // captured low-precision graphs are found again); held until the end
+    std::lock_guard<std::recursive_mutex> lk(gb::mixed_device_mutex());
     char *mem = nullptr;
-    GB_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&mem), x_off + x_bytes, pool, s));
+    GB_TRY(gb::mixed_workspace(x_off + x_bytes, s, &mem));
     char *ws = mem;
     double *Ad = reinterpret_cast<double *>(mem + a_off);
     double *Bd = reinterpret_cast<double *>(mem + b_off);
@@ -217,10 +218,9 @@ extern "C" int gb_dtrsm_mixed_host(int side, int uplo, int trans, int diag, int6
     } while (0);
     if (iters_out) *iters_out = it_max;
     if (est_err_out) *est_err_out = est_max;
-    // the copy stream must be done with the device buffers before they go
-    // back to the pool
+    // the copy stream must be done with the device buffers before the work
+    // space is used again
     if (ev_done && cudaEventRecord(ev_done, cs) == cudaSuccess) cudaStreamWaitEvent(s, ev_done, 0);
-    cudaFreeAsync(mem, s);
     const int c = gb::check(cudaStreamSynchronize(s));
     if (!st && c) st = c;
     if (ev_a) cudaEventDestroy(ev_a);

@@ -16,6 +16,11 @@ synthetic):
 With the diagonal >= 1 and each row's off-diagonal absolute sum < 1, A is
 strictly diagonally dominant, hence well conditioned.
 
+Device recipe (``make_problem_device``, for sizes whose host generation would
+be slow, e.g. k = 32768): the same distributions drawn on the GPU by a torch
+generator seeded with ``seed`` (a different stream of numbers than the host
+recipe), the unreferenced triangle zero.
+
 Batched recipe: ``SeedSequence(seed).spawn(count)``; per instance
 m = round(exp(U(ln 16, ln 512))), n = integers(1, 257), side and uplo uniform
 over {0, 1}, trans = NoTrans, diag = NonUnit, alpha = 1.
@@ -73,3 +78,23 @@ def make_batch(count, seed):
         items.append(dict(side=side, uplo=uplo, trans=NOTRANS, diag=NONUNIT,
                           m=m, n=n, alpha=1.0, A=A, B=B))
     return items
+
+
+def make_problem_device(side, uplo, trans, diag, m, n, seed):
+    """(A, B) as column-major torch FP64 CUDA tensors with the distributions
+    of ``make_problem`` (different random numbers), generated on the GPU."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed))
+    k = m if side == LEFT else n
+    # column-major k x k: the transpose of a row-major buffer
+    A = torch.empty((k, k), dtype=torch.float64, device="cuda").t()
+    A.uniform_(-1.0, 1.0, generator=g).div_(max(k, 1))
+    A.diagonal().uniform_(1.0, 2.0, generator=g)
+    if uplo == LOWER:
+        A.copy_(torch.tril(A))
+    else:
+        A.copy_(torch.triu(A))
+    B = torch.empty((n, m), dtype=torch.float64, device="cuda").t()
+    B.normal_(generator=g)
+    return A, B

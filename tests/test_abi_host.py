@@ -209,3 +209,19 @@ def test_mixed_host_copies_about_half_of_a_at_scale(lib):
     h2d, d2h = api.gb_mixed_host_bytes(0, 0, k, k)
     a = h2d - k * k * 8
     assert 0.5 * k * k * 8 < a < 0.51 * k * k * 8
+
+
+@pytest.mark.parametrize("model", ["recursive", "iterative", "blocked"])
+def test_comp_formulas_match_hand_values(model):
+    """Comp(i) of the three computation models (Section V-A, V-B, V-C) against
+    values worked out by hand for distinct stub task times, i = 0..3."""
+    g = _golden()["comp_hand_values"]
+    TS = lambda i: g["TS"][i]  # noqa: E731
+    for i in range(4):
+        if model == "recursive":
+            got = models.recursive_comp(i, TS, lambda j: g["gemm_recursive"][j])
+        elif model == "iterative":
+            got = models.iterative_comp(i, TS, lambda i_, j: 100.0 * i_ + j + 1)
+        else:
+            got = models.blocked_comp(i, TS, lambda i_: g["gemm_blocked"][i_])
+        assert got == g[model][str(i)], (model, i, got)

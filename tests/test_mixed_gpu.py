@@ -88,6 +88,24 @@ def test_mixed_config_scale_sampled(m, n):
     assert fwd_err(X, Xo) <= 1e-10
 
 
+@pytest.mark.parametrize("m,n", [(16384, 16384), (32768, 4096)])
+def test_mixed_fp8_config_scale_sampled(m, n):
+    """FP8 E4M3 updates (per-128x128-block power-of-two scales) at the
+    mixed-precision configuration sizes: sampled right-hand sides vs the
+    oracle within 1e-10; the refinement step count is bounded and reported."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    A, B = inputs.make_problem_device(0, 0, 0, 0, m, n, seed=7)
+    cols = [0, 5, n // 2, n - 1]
+    Bs = B[:, cols].cpu().numpy()
+    st, it, est = api.trsm_mixed(0, 0, 0, 0, 1.5, A, B, tol=1e-11, prec=api.PREC_FP8, max_iter=60)
+    torch.cuda.synchronize()
+    hist = api.gb_mixed_history()
+    assert st == 0 and 1 <= it <= 12, (st, it, est, hist)
+    Xo = oracle.dtrsm(0, 0, 0, 0, 1.5, A.cpu().numpy(), Bs)
+    assert fwd_err(B[:, cols].cpu().numpy(), Xo) <= 1e-10, (it, hist)
+
+
 @pytest.mark.parametrize("side,uplo,trans,diag", [(0, 0, 0, 0), (1, 1, 1, 0), (0, 1, 0, 1), (1, 0, 1, 1)])
 def test_mixed_fp8_block_scaled_updates(side, uplo, trans, diag):
     """FP8 E4M3 GEMM updates with per-block power-of-two scales: the

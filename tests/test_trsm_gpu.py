@@ -107,3 +107,40 @@ def test_config_scale_sampled_columns():
     assert fwd_err(X, Xo) <= 1e-12
     eta = bwd_err(0, 0, 0, 0, 1.5, A, B[:, cols], X)
     assert eta <= 10 * m * U64
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", [(s, u, t, d) for s in (0, 1) for u in (0, 1) for t in (0, 1)
+                                                  for d in (0, 1)])
+def test_plain_8192_all_forms_sampled(side, uplo, trans, diag):
+    """m = n = 8192, alpha = 1.5, every side/uplo/trans/diag form with the
+    planner's default plan: sampled columns (side Left) or rows (side Right,
+    where each row of X depends only on its row of B), first, middle and
+    last, vs the oracle; forward error <= 1e-12, backward error <= 10 k u."""
+    _plain_sampled(side, uplo, trans, diag, 8192, 8192, seed=40 + 8 * side + 4 * uplo + 2 * trans + diag)
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", [(1, 1, 1, 1), (0, 1, 1, 0)])
+def test_plain_16384_right_and_transposed_upper_sampled(side, uplo, trans, diag):
+    """m = n = 16384 in a Right-side and a transposed Upper form (the last
+    rows / columns of X included)."""
+    _plain_sampled(side, uplo, trans, diag, 16384, 16384, seed=60 + side)
+
+
+def _plain_sampled(side, uplo, trans, diag, m, n, seed):
+    import torch
+    from paper_2305_19917_gb300 import api
+    A, B = inputs.make_problem_device(side, uplo, trans, diag, m, n, seed)
+    if side == 0:
+        idx = [0, 1, n // 2, n - 2, n - 1]
+        Bs = B[:, idx].cpu().numpy()
+    else:
+        idx = [0, 1, m // 2, m - 2, m - 1]
+        Bs = B[idx, :].cpu().numpy()
+    api.trsm(side, uplo, trans, diag, 1.5, A, B)
+    torch.cuda.synchronize()
+    Xs = B[:, idx].cpu().numpy() if side == 0 else B[idx, :].cpu().numpy()
+    Ah = A.cpu().numpy()
+    Xo = oracle.dtrsm(side, uplo, trans, diag, 1.5, Ah, Bs)
+    assert fwd_err(Xs, Xo) <= 1e-12
+    k = m if side == 0 else n
+    assert bwd_err(side, uplo, trans, diag, 1.5, Ah, Bs, Xs) <= 10 * k * U64
