@@ -15,6 +15,9 @@ Contents
   * ``mlp``        -- FP64 forward/backward/Adam of the cost-model MLP.
   * ``models``     -- the paper's computation models (Section V): refinement
                       level, stop rule, task counts and Comp(i) formulas.
+  * ``dpotrf``     -- plain Cholesky-Crout factorisation (C, ``potrf_oracle.c``),
+                      the factorisation the paper names as the next user of its
+                      solver (Section VIII).
 """
 import ctypes
 import os
@@ -47,6 +50,8 @@ def lib():
         l.oracle_mlp_loss_grad.restype = dbl
         l.oracle_adam.argtypes = [pd, pd, pd, pd, i64, dbl, dbl, dbl, dbl, ip]
         l.oracle_adam.restype = None
+        l.oracle_dpotrf.argtypes = [ip, i64, pd, i64]
+        l.oracle_dpotrf.restype = i64
         _lib = l
     return _lib
 
@@ -118,6 +123,21 @@ def op_dense(uplo, trans, diag, A, k):
     T = np.where(mask, A, 0.0)
     T[np.diag_indices(k)] = 1.0 if diag == 1 else np.diagonal(A)
     return T.T.copy() if trans == 1 else T
+
+
+def dpotrf(uplo, A):
+    """(F, info): the Cholesky factor of the symmetric positive definite A
+    (uplo 0: lower L with A = L L^T; 1: upper U with A = U^T U) written over
+    the named triangle of a column-major copy of A (the other triangle is
+    copied unchanged); info = 0, or j + 1 when column j has a non-positive
+    pivot (LAPACK convention)."""
+    F = _fortran64(A).copy(order="F")
+    n = F.shape[0]
+    assert F.shape[1] == n
+    info = lib().oracle_dpotrf(int(uplo), n, _ptr(F), max(1, n))
+    if info < 0:
+        raise ValueError(f"oracle_dpotrf: invalid argument {-info}")
+    return F, int(info)
 
 
 # ---- cost-model network (FP64) ---------------------------------------------------

@@ -10,7 +10,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
-SOURCES = ["trsm_oracle.c", "mlp_oracle.c"]
+SOURCES = ["trsm_oracle.c", "mlp_oracle.c", "potrf_oracle.c"]
 
 
 def build(force: bool = False) -> str:

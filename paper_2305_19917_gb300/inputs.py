@@ -21,6 +21,12 @@ be slow, e.g. k = 32768): the same distributions drawn on the GPU by a torch
 generator seeded with ``seed`` (a different stream of numbers than the host
 recipe), the unreferenced triangle zero.
 
+Cholesky recipe (``make_spd``, ``make_spd_device``): a symmetric A with the
+triangle recipe's entries, off-diagonal (U(-1, 1) + U(-1, 1)^T) / (2k) and
+diagonal U[1, 2), so every row's off-diagonal absolute sum is below the
+diagonal: symmetric, strictly diagonally dominant with a positive diagonal,
+hence positive definite and well conditioned; both triangles are stored.
+
 Batched recipe: ``SeedSequence(seed).spawn(count)``; per instance
 m = round(exp(U(ln 16, ln 512))), n = integers(1, 257), side and uplo uniform
 over {0, 1}, trans = NoTrans, diag = NonUnit, alpha = 1.
@@ -98,3 +104,24 @@ def make_problem_device(side, uplo, trans, diag, m, n, seed):
     B = torch.empty((n, m), dtype=torch.float64, device="cuda").t()
     B.normal_(generator=g)
     return A, B
+
+
+def make_spd(k, seed):
+    """Symmetric positive definite k x k FP64 (column-major), both triangles."""
+    rng = np.random.default_rng(seed)
+    off = rng.uniform(-1.0, 1.0, size=k * k).reshape((k, k), order="F") / max(k, 1)
+    A = np.asfortranarray((off + off.T) / 2.0)
+    A[np.diag_indices(k)] = rng.uniform(1.0, 2.0, size=k)
+    return A
+
+
+def make_spd_device(k, seed):
+    """As make_spd, drawn on the GPU (torch generator; different numbers)."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed))
+    A = torch.empty((k, k), dtype=torch.float64, device="cuda").t()
+    A.uniform_(-1.0, 1.0, generator=g).div_(max(k, 1))
+    A.add_(A.t().clone()).mul_(0.5)
+    A.diagonal().uniform_(1.0, 2.0, generator=g)
+    return A
