@@ -165,6 +165,22 @@ int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m,
                    int *iters_out, double *est_err_out, void *stream);
 
 /*
+ * gb_dtrsm_mixed_leaf: gb_dtrsm_mixed with an explicit plan for its
+ * low-precision solve: `leaf` (argument 15, after max_iter; iters_out,
+ * est_err_out and stream follow as arguments 16-18) is the order of the
+ * recursion's leaves (Section V-A: refinement level ~ k / leaf), a multiple
+ * of 128 in [128, 8192], or 0 for the default (1024 rows for BF16, each leaf
+ * one tensor-core kernel launch; 128 rows for FP8, larger FP8 leaves are
+ * solved blocked in 128-row steps).  Any other value returns -15.  Results
+ * and status codes as gb_dtrsm_mixed; the planner's timing sweep uses it.
+ */
+int gb_dtrsm_mixed_leaf(int side, int uplo, int trans, int diag, int64_t m,
+                        int64_t n, double alpha, const double *A, int64_t lda,
+                        double *B, int64_t ldb, double tol, int prec,
+                        int max_iter, int64_t leaf, int *iters_out,
+                        double *est_err_out, void *stream);
+
+/*
  * gb_dtrsm_mixed_noalloc: gb_dtrsm_mixed for callers that cannot allocate
  * device memory (the paper has no counterpart; this is an interface
  * addition).  Same arguments, results and status codes as gb_dtrsm_mixed
@@ -222,6 +238,51 @@ int gb_dtrsm_mixed_host(int side, int uplo, int trans, int diag,
  * and sizes.  Host-only; -1 for negative sizes.
  */
 int64_t gb_mixed_host_bytes(int side, int uplo, int64_t m, int64_t n, int64_t *d2h_bytes);
+
+/*
+ * gb_gemm_update: the plain path's gemm task on its own (Section IV stage 2,
+ * b.low -= L.mid x.up, with many right-hand sides): C = alpha*C - A*B with
+ * A (M x K, lda), B (K x N, ldb) and C (M x N, ldc) column-major device
+ * arrays of FP64 (dtype 0) or FP32 (dtype 1), alpha converted to the dtype;
+ * DFMA / FFMA register-blocked kernel, asynchronous on `stream`.  The
+ * planner's analytic model times it (gemm(j) of Section V).  Returns 0, -1
+ * for a bad dtype, -2..-4 for negative M, N, K, -5 / -7 / -9 for a NULL
+ * operand that is needed, -6 / -8 / -10 for a leading dimension below its
+ * operand's row count, or GB_STATUS_CUDA_ERROR.
+ */
+int gb_gemm_update(int dtype, int64_t M, int64_t N, int64_t K, const void *A,
+                   int64_t lda, const void *B, int64_t ldb, void *C,
+                   int64_t ldc, double alpha, void *stream);
+
+/*
+ * gb_dpotrf / gb_spotrf: Cholesky factorisation on this library's
+ * triangular solve -- the use the paper names for its TS machinery (Section
+ * VIII, future work), with the recursive computation model of Section V-A:
+ * split A's order in two (first part a multiple of 64), factorise the first
+ * diagonal block, solve the off-diagonal panel against it with gb_dtrsm /
+ * gb_strsm (side Right, Lower, transposed: L21 = A21 L11^-T; or side Left,
+ * Upper, transposed: U12 = U11^-T A12), update the trailing block by a SYRK
+ * (A22 -= L21 L21^T, or U12^T U12; its triangle only), recurse; leaves of at
+ * most 64 columns are factorised by one CTA in shared memory.
+ *   1 uplo   GB_LOWER: A = L L^T, L over the lower triangle;
+ *            GB_UPPER: A = U^T U, U over the upper triangle
+ *   2 n      order of A, >= 0
+ *   3 A      device, column-major n x n, symmetric positive definite; only
+ *            the named triangle is read and overwritten (the other is not
+ *            touched)
+ *   4 lda    >= max(1, n)
+ *   5 info   host, out: 0 on success, or j (1-based) when the leading
+ *            minor of order j is not positive definite (a pivot <= 0 or
+ *            NaN; the LAPACK ?potrf convention).  With info > 0 the
+ *            factorisation stopped: columns from j on are undefined.
+ *   6 stream
+ * Returns 0 (then see *info), -i for invalid argument i, or
+ * GB_STATUS_CUDA_ERROR.  Synchronous (it reads info); a 4-byte device word
+ * for info comes from the library's stream-ordered pool.  Accuracy (FP64):
+ * ||A - L L^T|| / ||A|| is a small multiple of n 2^-53.
+ */
+int gb_dpotrf(int uplo, int64_t n, double *A, int64_t lda, int64_t *info, void *stream);
+int gb_spotrf(int uplo, int64_t n, float *A, int64_t lda, int64_t *info, void *stream);
 
 /*
  * gb_mixed_workspace_release: frees the cached work space of gb_dtrsm_mixed

@@ -58,6 +58,11 @@ _SIGS = {
                              ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
     "gb_mixed_host_bytes": ([i32, i32, i64, i64, ctypes.POINTER(i64)], i64),
     "gb_mixed_workspace_release": ([vp], i32),
+    "gb_dpotrf": ([i32, i64, vp, i64, ctypes.POINTER(i64), vp], i32),
+    "gb_dtrsm_mixed_leaf": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32, i64,
+                             ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
+    "gb_gemm_update": ([i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, dbl, vp], i32),
+    "gb_spotrf": ([i32, i64, vp, i64, ctypes.POINTER(i64), vp], i32),
     "gb_trsm_batched": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "gb_batched_plan_create": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                 ctypes.POINTER(vp)], i32),
@@ -178,6 +183,57 @@ def gb_mixed_host_bytes(side, uplo, m, n):
     d2h = i64()
     h2d = lib().gb_mixed_host_bytes(side, uplo, m, n, ctypes.byref(d2h))
     return int(h2d), int(d2h.value)
+
+
+def gb_dtrsm_mixed_leaf(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, leaf,
+                        stream=0):
+    """gb_dtrsm_mixed with an explicit leaf order.  Returns (status, iters, est_err)."""
+    it, est = i32(), dbl()
+    st = lib().gb_dtrsm_mixed_leaf(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, leaf,
+                                   ctypes.byref(it), ctypes.byref(est), stream or None)
+    return st, it.value, est.value
+
+
+def gb_gemm_update(dtype, M, N, K, A, lda, B, ldb, C, ldc, alpha, stream=0):
+    return lib().gb_gemm_update(dtype, M, N, K, A, lda, B, ldb, C, ldc, alpha, stream or None)
+
+
+def gb_dpotrf(uplo, n, A, lda, stream=0):
+    """Returns (status, info)."""
+    info = i64()
+    st = lib().gb_dpotrf(uplo, n, A, lda, ctypes.byref(info), stream or None)
+    return st, info.value
+
+
+def gb_spotrf(uplo, n, A, lda, stream=0):
+    """Returns (status, info)."""
+    info = i64()
+    st = lib().gb_spotrf(uplo, n, A, lda, ctypes.byref(info), stream or None)
+    return st, info.value
+
+
+def potrf(uplo, A, stream=None):
+    """Cholesky factorisation in place on a torch float64 / float32 CUDA
+    tensor (column-major, n x n): the named triangle is overwritten by the
+    factor.  Returns info (0, or the order of the first leading minor that is
+    not positive definite); raises GbError on argument / CUDA errors."""
+    import torch
+    n = A.shape[0]
+    if A.dim() != 2 or A.shape[1] != n:
+        raise ValueError("A must be square")
+    pa, lda = _colmajor(A, "A")
+    s = _stream_handle(stream)
+    if A.dtype == torch.float64:
+        st, info = gb_dpotrf(uplo, n, pa, lda, s)
+        fn = "gb_dpotrf"
+    elif A.dtype == torch.float32:
+        st, info = gb_spotrf(uplo, n, pa, lda, s)
+        fn = "gb_spotrf"
+    else:
+        raise TypeError(f"unsupported dtype {A.dtype}")
+    if st != 0:
+        raise GbError(fn, st)
+    return info
 
 
 def gb_mixed_workspace_release(stream=0):

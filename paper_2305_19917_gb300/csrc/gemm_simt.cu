@@ -206,6 +206,37 @@ int launch_gemm_update(const Canon<T> &c, int64_t ci0, int64_t M, int64_t ak0, i
 template int launch_gemm_update<double>(const Canon<double> &, int64_t, int64_t, int64_t, int64_t, double);
 template int launch_gemm_update<float>(const Canon<float> &, int64_t, int64_t, int64_t, int64_t, float);
 
+}  // namespace gb
+
+// The gemm task on its own, column-major operands: C (M x N, ldc) =
+// alpha*C - A (M x K, lda) * B (K x N, ldb), FP64 (dtype 0) or FP32 (1) --
+// the kernel every plain solve uses for its off-diagonal updates.
+extern "C" int gb_gemm_update(int dtype, int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B,
+                              int64_t ldb, void *C, int64_t ldc, double alpha, void *stream)
+{
+    if (dtype != 0 && dtype != 1) return -1;
+    if (M < 0) return -2;
+    if (N < 0) return -3;
+    if (K < 0) return -4;
+    if (A == nullptr && M * K > 0) return -5;
+    if (lda < (M > 1 ? M : 1)) return -6;
+    if (B == nullptr && K * N > 0) return -7;
+    if (ldb < (K > 1 ? K : 1)) return -8;
+    if (C == nullptr && M * N > 0) return -9;
+    if (ldc < (M > 1 ? M : 1)) return -10;
+    if (M == 0 || N == 0) return 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dtype == 0)
+        return gb::launch_cfg<double, true, true>(M, N, K, static_cast<const double *>(A), lda,
+                                                  static_cast<const double *>(B), ldb, static_cast<double *>(C), ldc,
+                                                  alpha, s);
+    return gb::launch_cfg<float, true, true>(M, N, K, static_cast<const float *>(A), lda,
+                                             static_cast<const float *>(B), ldb, static_cast<float *>(C), ldc,
+                                             float(alpha), s);
+}
+
+namespace gb {
+
 // ---- alpha == 0: Bv = 0 ------------------------------------------------------
 namespace {
 template <typename T>

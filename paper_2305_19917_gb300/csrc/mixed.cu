@@ -64,7 +64,7 @@ constexpr int kSlices = 6;     // digit slices of Mv (8 bits each)
 // place from then on.
 constexpr int kZSlots = 3;
 constexpr int kBand = 128;     // FP32 band of diagonal 128-blocks (column-major per block)
-constexpr int kLeaf = 1024;    // leaf order of the BF16 low-precision solve (one leaf kernel launch each)
+constexpr int kLeaf = 1024;    // default leaf order of the BF16 low-precision solve (one leaf kernel launch each)
 
 // Library fallback of the integer-built conversions below, for results
 // outside the normal double range.  Kept out of line: inlined, the compiler
@@ -908,13 +908,14 @@ struct LowExec {
     uint8_t *Y8 = nullptr;
     float *sY = nullptr;         // (kp/128) x (np/64) block scales of Y8
     const __nv_bfloat16 *binv16 = nullptr;  // two-term BF16 split of the inverses (tensor-core TS task)
+    int64_t leaf = 0;   // leaf order of the recursion (0 = the form's default)
     int status = 0;
     bool ok() const { return status == 0; }
     void ts(int64_t b0, int64_t nr, float a)
     {
         if (status) return;
         if (!fp8) {
-            // BF16 form: a leaf of up to kLeaf rows, left-looking, in one
+            // BF16 form: a leaf (kLeaf rows by default), left-looking, in one
             // launch: each 128-row block takes its update from the solved
             // blocks of the leaf and its TS task
             status = launch_leaf_tc(Abf, binv16, kp, np, b0, nr, Y, Ybf, s, status_word);
@@ -941,11 +942,13 @@ struct LowExec {
     }
 };
 
-// Recursive model (Section V-A) down to leaves of kLeaf rows (BF16 form:
-// each solved left-looking by one leaf kernel launch) or kBand rows (FP8 form).
+// Recursive model (Section V-A) down to leaves of e.leaf rows, by default
+// kLeaf (BF16 form: each leaf solved left-looking by one leaf kernel launch)
+// or kBand (FP8 form: larger leaves are solved blocked in kBand steps).
 int low_solve(LowExec &e, int64_t kp)
 {
-    drive_recursive(e, 0, kp, 24, (int64_t)(e.fp8 ? kBand : kLeaf), 1.0f, true);
+    const int64_t leaf = e.leaf > 0 ? e.leaf : (e.fp8 ? kBand : kLeaf);
+    drive_recursive(e, 0, kp, 24, leaf, 1.0f, true);
     return e.status;
 }
 
@@ -1006,6 +1009,7 @@ struct LowGraph {
     const void *ws = nullptr;
     int64_t kp = 0, np = 0;
     bool fp8 = false;
+    int64_t leaf = 0;
     uint64_t nkernels = 0;
     uint64_t used = 0;  // last use (LRU clock)
 };
@@ -1095,7 +1099,7 @@ int low_graph(LowExec &le, const void *ws, LowGraph **out)
     int victim = 0;
     for (int i = 0; i < kGraphs; i++) {
         LowGraph &c = cache[dev][i];
-        if (c.exec && c.ws == ws && c.kp == le.kp && c.np == le.np && c.fp8 == le.fp8) {
+        if (c.exec && c.ws == ws && c.kp == le.kp && c.np == le.np && c.fp8 == le.fp8 && c.leaf == le.leaf) {
             c.used = ++clock[dev];
             *out = &c;
             return 0;
@@ -1134,6 +1138,7 @@ int low_graph(LowExec &le, const void *ws, LowGraph **out)
     g.kp = le.kp;
     g.np = le.np;
     g.fp8 = le.fp8;
+    g.leaf = le.leaf;
     g.nkernels = capture_count() - before;
     g.used = ++clock[dev];
     *out = &g;
@@ -1275,7 +1280,7 @@ int mixed_prep_a(int side, int uplo, int trans, int diag, int64_t k, const doubl
 int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, double alpha, const double *B,
                   int64_t ldb, double *Bout, int64_t ldbo, double tol, int prec, int max_iter, int *iters_out,
                   double *est_err_out, cudaStream_t s, char *ws, const MixedLayout &L, bool use_graph,
-                  cudaEvent_t b_ready, bool merge_hist)
+                  cudaEvent_t b_ready, bool merge_hist, int64_t leaf)
 {
     const bool forward = mixed_forward(side, uplo, trans);
     const int64_t kp = L.kp, np = L.np;
@@ -1335,6 +1340,7 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
         le.sA = bf.bscale;
         le.Y8 = bf.Y8;
         le.sY = bf.sY;
+        le.leaf = leaf;
         LowGraph *lg = nullptr;
         if (use_graph) {
             graph_lock.lock();  // held until the solve returns
@@ -1447,7 +1453,7 @@ int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, doubl
 
 int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
                int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
-               double *est_err_out, cudaStream_t s, char *ws, bool use_graph, cudaEvent_t b_ready)
+               double *est_err_out, cudaStream_t s, char *ws, bool use_graph, cudaEvent_t b_ready, int64_t leaf)
 {
     const int64_t k = side == GB_LEFT ? m : n;
     const int64_t ncols = side == GB_LEFT ? n : m;
@@ -1457,21 +1463,21 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
     if (est_err_out) *est_err_out = 0;
     GB_TRY(mixed_prep_a(side, uplo, trans, diag, k, A, lda, prec, L, ws, s));
     return mixed_solve_b(side, uplo, trans, k, ncols, alpha, B, ldb, B, ldb, tol, prec, max_iter, iters_out,
-                         est_err_out, s, ws, L, use_graph, b_ready, false);
+                         est_err_out, s, ws, L, use_graph, b_ready, false, leaf);
 }
 
 cudaMemPool_t mixed_pool() { return library_pool(); }
 
 int dtrsm_mixed_impl(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
                      int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
-                     double *est_err_out, cudaStream_t s)
+                     double *est_err_out, cudaStream_t s, int64_t leaf)
 {
     const MixedLayout L = mixed_layout(side, m, n, prec);
     std::lock_guard<std::recursive_mutex> lk(mixed_device_mutex());
     char *ws = nullptr;
     GB_TRY(mixed_workspace(L.total, s, &ws));
     return mixed_core(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, iters_out,
-                      est_err_out, s, ws, true, nullptr);
+                      est_err_out, s, ws, true, nullptr, leaf);
 }
 
 }  // namespace gb
@@ -1509,9 +1515,9 @@ int mixed_validate(int side, int uplo, int trans, int diag, int64_t m, int64_t n
 }
 }  // namespace gb
 
-extern "C" int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
-                              const double *A, int64_t lda, double *B, int64_t ldb, double tol, int prec,
-                              int max_iter, int *iters_out, double *est_err_out, void *stream)
+static int dtrsm_mixed_entry(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
+                             const double *A, int64_t lda, double *B, int64_t ldb, double tol, int prec,
+                             int max_iter, int64_t leaf, int *iters_out, double *est_err_out, void *stream)
 {
     if (iters_out) *iters_out = 0;
     if (est_err_out) *est_err_out = 0;
@@ -1532,5 +1538,26 @@ extern "C" int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m
         return gb::check(cudaStreamSynchronize(s));
     }
     return gb::dtrsm_mixed_impl(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, iters_out,
-                                est_err_out, s);
+                                est_err_out, s, leaf);
+}
+
+extern "C" int gb_dtrsm_mixed(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
+                              const double *A, int64_t lda, double *B, int64_t ldb, double tol, int prec,
+                              int max_iter, int *iters_out, double *est_err_out, void *stream)
+{
+    return dtrsm_mixed_entry(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, 0,
+                             iters_out, est_err_out, stream);
+}
+
+extern "C" int gb_dtrsm_mixed_leaf(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
+                                   const double *A, int64_t lda, double *B, int64_t ldb, double tol, int prec,
+                                   int max_iter, int64_t leaf, int *iters_out, double *est_err_out, void *stream)
+{
+    if (leaf != 0 && (leaf < 128 || leaf > 8192 || leaf % 128 != 0)) {
+        if (iters_out) *iters_out = 0;
+        if (est_err_out) *est_err_out = 0;
+        return -15;
+    }
+    return dtrsm_mixed_entry(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, leaf,
+                             iters_out, est_err_out, stream);
 }

@@ -28,7 +28,8 @@ MixedLayout mixed_layout(int side, int64_t m, int64_t n, int prec);
 // not).  Arguments are assumed valid; alpha != 0; m, n > 0.  Synchronous.
 int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha, const double *A,
                int64_t lda, double *B, int64_t ldb, double tol, int prec, int max_iter, int *iters_out,
-               double *est_err_out, cudaStream_t s, char *ws, bool use_graph, cudaEvent_t b_ready);
+               double *est_err_out, cudaStream_t s, char *ws, bool use_graph, cudaEvent_t b_ready,
+               int64_t leaf = 0);
 // The two halves of mixed_core, for callers that solve several column blocks
 // of one problem against one preparation of A (the work space laid out for
 // the widest block, L.np >= every block's ncols):
@@ -39,12 +40,14 @@ int mixed_core(int side, int uplo, int trans, int diag, int64_t m, int64_t n, do
 //    the user's orientation (columns of B for side = left, rows for right).
 //    merge_hist folds this block's refinement history into the previous
 //    block's (step-wise maximum) instead of starting a new one.
+// leaf: order of the low-precision solve's recursion leaves (a multiple of
+// 128; 0 = the form's default, 1024 rows BF16 / 128 rows FP8).
 int mixed_prep_a(int side, int uplo, int trans, int diag, int64_t k, const double *A, int64_t lda, int prec,
                  const MixedLayout &L, char *ws, cudaStream_t s);
 int mixed_solve_b(int side, int uplo, int trans, int64_t k, int64_t ncols, double alpha, const double *B,
                   int64_t ldb, double *Bout, int64_t ldbo, double tol, int prec, int max_iter, int *iters_out,
                   double *est_err_out, cudaStream_t s, char *ws, const MixedLayout &L, bool use_graph,
-                  cudaEvent_t b_ready, bool merge_hist);
+                  cudaEvent_t b_ready, bool merge_hist, int64_t leaf = 0);
 // The library's stream-ordered memory pool for work space (current device).
 cudaMemPool_t mixed_pool();
 // Per-device lock of the mixed solves that use cached graphs or the cached
