@@ -240,6 +240,20 @@ int gb_dtrsm_mixed_host(int side, int uplo, int trans, int diag,
 int64_t gb_mixed_host_bytes(int side, int uplo, int64_t m, int64_t n, int64_t *d2h_bytes);
 
 /*
+ * gb_set_lookahead: switch the plain solves' lookahead on (1, the default)
+ * or off (0) for the whole process; any other value only queries.  With it,
+ * an off-diagonal update whose rows extend beyond the next diagonal block is
+ * split: the next block's rows are updated first on the caller's stream, so
+ * that block's TS task starts at once, while the other rows are updated on a
+ * library stream at the same time (the overlap of diagonal solves and
+ * updates of Sections V-C and VIII); the solve joins that stream before it
+ * returns, so results and stream semantics are unchanged.  Used by the
+ * blocked and recursive models when the order exceeds four blocks.  Returns
+ * the previous setting.  Host only.
+ */
+int gb_set_lookahead(int on);
+
+/*
  * gb_gemm_update: the plain path's gemm task on its own (Section IV stage 2,
  * b.low -= L.mid x.up, with many right-hand sides): C = alpha*C - A*B with
  * A (M x K, lda), B (K x N, ldb) and C (M x N, ldc) column-major device
@@ -384,6 +398,29 @@ int gb_plan_features(int dtype, int side, int uplo, int trans, int64_t m,
 int gb_plan_set_model(const char *path);
 int gb_plan_choose(int dtype, int side, int uplo, int trans, int64_t m,
                    int64_t n, gb_plan *plan_out, double *predicted_ms);
+
+/*
+ * gb_plan_mixed_candidates: the mixed-precision candidates of the precision
+ * decision for an order-k triangle (host only): (prec[i], leaf[i]) for
+ * i < 5 -- BF16 with leaves of 512, 1024, 2048 rows, FP8 with 128 and 512 --
+ * and plans[i], their encoding for the cost model (driver recursive, nb =
+ * leaf, depth = log2(kp / leaf) clamped to 0..6, kp = k rounded up to 128).
+ * Any output may be NULL; at most `cap` entries are written.  Returns 5, or
+ * -1 for k < 0, -5 for cap < 0.
+ *
+ * gb_plan_choose_precision: the planner's answer for a solve to FP64-level
+ * accuracy: the plain FP64 path with the network's best plan, or one of the
+ * mixed candidates above (gb_dtrsm_mixed_leaf with that precision and
+ * leaf), whichever the loaded network predicts fastest.  *prec_out = -1
+ * (plain FP64), GB_PREC_BF16 or GB_PREC_FP8; *leaf_out = the leaf (0 for
+ * plain); plan_out (optional) = the plain plan or the candidate's encoding;
+ * predicted_ms (optional).  Arguments 1-5 as gb_plan_choose's 2-6; returns 0,
+ * -i for invalid argument i (-6: prec_out or leaf_out NULL), or
+ * GB_STATUS_NO_MODEL (then plain FP64 with the built-in default plan).
+ */
+int gb_plan_mixed_candidates(int64_t k, int *prec, int64_t *leaf, gb_plan *plans, int cap);
+int gb_plan_choose_precision(int side, int uplo, int trans, int64_t m, int64_t n, int *prec_out,
+                             int64_t *leaf_out, gb_plan *plan_out, double *predicted_ms);
 int gb_autotune_time(int dtype, int side, int uplo, int trans, int diag,
                      int64_t m, int64_t n, double alpha, const void *A,
                      int64_t lda, void *B, int64_t ldb, const gb_plan *plans,

@@ -62,6 +62,7 @@ _SIGS = {
     "gb_dtrsm_mixed_leaf": ([i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, dbl, i32, i32, i64,
                              ctypes.POINTER(i32), ctypes.POINTER(dbl), vp], i32),
     "gb_gemm_update": ([i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, dbl, vp], i32),
+    "gb_set_lookahead": ([i32], i32),
     "gb_spotrf": ([i32, i64, vp, i64, ctypes.POINTER(i64), vp], i32),
     "gb_trsm_batched": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "gb_batched_plan_create": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
@@ -74,6 +75,9 @@ _SIGS = {
     "gb_plan_features": ([i32, i32, i32, i32, i64, i64, ctypes.POINTER(GbPlan), ctypes.POINTER(flt)], i32),
     "gb_plan_set_model": ([ctypes.c_char_p], i32),
     "gb_plan_choose": ([i32, i32, i32, i32, i64, i64, ctypes.POINTER(GbPlan), ctypes.POINTER(dbl)], i32),
+    "gb_plan_mixed_candidates": ([i64, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(GbPlan), i32], i32),
+    "gb_plan_choose_precision": ([i32, i32, i32, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                  ctypes.POINTER(GbPlan), ctypes.POINTER(dbl)], i32),
     "gb_autotune_time": ([i32, i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, ctypes.POINTER(GbPlan), i32,
                           i32, ctypes.POINTER(dbl), vp], i32),
     "gb_autotune": ([i32, i32, i32, i32, i32, i64, i64, dbl, vp, i64, vp, i64, ctypes.POINTER(GbPlan),
@@ -192,6 +196,11 @@ def gb_dtrsm_mixed_leaf(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, to
     st = lib().gb_dtrsm_mixed_leaf(side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tol, prec, max_iter, leaf,
                                    ctypes.byref(it), ctypes.byref(est), stream or None)
     return st, it.value, est.value
+
+
+def gb_set_lookahead(on):
+    """Plain solves' lookahead on (1) / off (0); -1 queries.  Returns the previous setting."""
+    return lib().gb_set_lookahead(on)
 
 
 def gb_gemm_update(dtype, M, N, K, A, lda, B, ldb, C, ldc, alpha, stream=0):
@@ -331,6 +340,24 @@ def gb_plan_choose(dtype, side, uplo, trans, m, n):
     p, ms = GbPlan(), dbl()
     st = lib().gb_plan_choose(dtype, side, uplo, trans, m, n, ctypes.byref(p), ctypes.byref(ms))
     return st, dict(driver=p.driver, nb=p.nb, depth=p.depth), ms.value
+
+
+def gb_plan_mixed_candidates(k):
+    """[(prec, leaf, plan dict), ...] of the precision decision for order k."""
+    prec = (i32 * 8)()
+    leaf = (i64 * 8)()
+    plans = (GbPlan * 8)()
+    n = lib().gb_plan_mixed_candidates(k, prec, leaf, plans, 8)
+    return [(prec[i], leaf[i], dict(driver=plans[i].driver, nb=plans[i].nb, depth=plans[i].depth))
+            for i in range(n)]
+
+
+def gb_plan_choose_precision(side, uplo, trans, m, n):
+    """(status, prec (-1 = plain FP64), leaf, plan dict, predicted ms)."""
+    pr, lf, p, ms = i32(), i64(), GbPlan(), dbl()
+    st = lib().gb_plan_choose_precision(side, uplo, trans, m, n, ctypes.byref(pr), ctypes.byref(lf),
+                                        ctypes.byref(p), ctypes.byref(ms))
+    return st, pr.value, lf.value, dict(driver=p.driver, nb=p.nb, depth=p.depth), ms.value
 
 
 def gb_autotune_time(dtype, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, plans, reps=2, stream=0):

@@ -193,6 +193,78 @@ int gb_plan_set_model(const char *path)
     return 0;
 }
 
+// The mixed-precision candidates of the precision decision: (low precision,
+// leaf order of its recursive low-precision solve), encoded for the network
+// as a recursive plan with nb = leaf and depth = log2(kp / leaf) (clamped to
+// 0..6), with the BF16-mixed / FP8-mixed dtype one-hot.
+static const int kMixedCand[5][2] = {{GB_PREC_BF16, 512}, {GB_PREC_BF16, 1024}, {GB_PREC_BF16, 2048},
+                                     {GB_PREC_FP8, 128}, {GB_PREC_FP8, 512}};
+
+int gb_plan_mixed_candidates(int64_t k, int *prec, int64_t *leaf, gb_plan *plans, int cap)
+{
+    if (k < 0) return -1;
+    if (cap < 0) return -5;
+    const int64_t kp = (k + 127) / 128 * 128;
+    int i = 0;
+    for (; i < 5 && i < cap; i++) {
+        const int64_t lf = kMixedCand[i][1];
+        int d = 0;
+        while (d < 6 && (lf << (d + 1)) <= kp) d++;
+        if (prec) prec[i] = kMixedCand[i][0];
+        if (leaf) leaf[i] = lf;
+        if (plans) plans[i] = {GB_DRIVER_RECURSIVE, int(lf), d, 0};
+    }
+    return 5;
+}
+
+int gb_plan_choose_precision(int side, int uplo, int trans, int64_t m, int64_t n, int *prec_out, int64_t *leaf_out,
+                             gb_plan *plan_out, double *predicted_ms)
+{
+    if (side != GB_LEFT && side != GB_RIGHT) return -1;
+    if (uplo != GB_LOWER && uplo != GB_UPPER) return -2;
+    if (trans != GB_NOTRANS && trans != GB_TRANS) return -3;
+    if (m < 0) return -4;
+    if (n < 0) return -5;
+    if (!prec_out || !leaf_out) return -6;
+    std::lock_guard<std::mutex> lk(gb::g_mu);
+    const int64_t k = side == GB_LEFT ? m : n;
+    if (!gb::g_model.loaded) {
+        *prec_out = -1;
+        *leaf_out = 0;
+        if (plan_out) *plan_out = gb::default_plan(0, k);
+        if (predicted_ms) *predicted_ms = -1.0;
+        return GB_STATUS_NO_MODEL;
+    }
+    gb_plan best_plain;
+    double t_plain = 0;
+    GB_TRY(gb::model_choose(0, side, uplo, trans, m, n, &best_plain, &t_plain));
+    int prec[5];
+    int64_t leaf[5];
+    gb_plan cand[5];
+    gb_plan_mixed_candidates(k, prec, leaf, cand, 5);
+    float feats[5 * gb::kFeat], pred[5];
+    for (int i = 0; i < 5; i++)
+        gb::plan_features(prec[i] == GB_PREC_BF16 ? gb::GB_DTYPE_BF16_MIXED : gb::GB_DTYPE_FP8_MIXED, side, uplo,
+                          trans, m, n, cand[i], &feats[i * gb::kFeat]);
+    GB_CUDA(cudaMemcpy(gb::g_model.dX, feats, sizeof(feats), cudaMemcpyHostToDevice));
+    GB_TRY(gb::mlp_forward(gb::g_model.dparams, gb::g_model.D, gb::g_model.dX, 5, gb::g_model.dY, nullptr, 0));
+    GB_CUDA(cudaMemcpy(pred, gb::g_model.dY, sizeof(pred), cudaMemcpyDeviceToHost));
+    int bi = -1;
+    double bt = t_plain;
+    for (int i = 0; i < 5; i++) {
+        const double t = std::exp(double(pred[i]) * gb::g_model.scale + gb::g_model.mean);
+        if (t < bt) {
+            bt = t;
+            bi = i;
+        }
+    }
+    *prec_out = bi < 0 ? -1 : prec[bi];
+    *leaf_out = bi < 0 ? 0 : leaf[bi];
+    if (plan_out) *plan_out = bi < 0 ? best_plain : cand[bi];
+    if (predicted_ms) *predicted_ms = bt;
+    return 0;
+}
+
 int gb_plan_choose(int dtype, int side, int uplo, int trans, int64_t m, int64_t n, gb_plan *plan_out,
                    double *predicted_ms)
 {

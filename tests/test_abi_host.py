@@ -225,3 +225,36 @@ def test_comp_formulas_match_hand_values(model):
         else:
             got = models.blocked_comp(i, TS, lambda i_: g["gemm_blocked"][i_])
         assert got == g[model][str(i)], (model, i, got)
+
+
+def test_paper_policy_uses_the_pinned_comp_formulas():
+    """The planner's Section V models (costmodel.PaperAnalyticPolicy) give the
+    same Comp as the pinned oracle formulas (oracle/models.py) for the same
+    task times, for the recursive, iterative and blocked models."""
+    from paper_2305_19917_gb300 import costmodel
+    k, ncols = 1024, 100
+    ts = {str(o): 0.01 * o ** 1.5 + 0.003 for o in (1024, 512, 256, 128, 64, 32, 16)}
+    gemm = {}
+    for j in range(6):
+        h = k // 2 ** (j + 1)
+        gemm[f"{h},{h}"] = 1e-4 * h * h / 64 + 0.002
+    for nb in (16, 64, 256):
+        r = k // nb
+        for c in range(1, r):
+            gemm[f"{nb},{c * nb}"] = 1e-4 * nb * c * nb / 64 + 0.002
+    comp = dict(dtype=0, side=0, uplo=0, trans=0, m=k, n=ncols, ts=ts, gemm=gemm)
+    pol = costmodel.PaperAnalyticPolicy({costmodel.shape_key(comp): comp})
+    base = dict(dtype=0, side=0, uplo=0, trans=0, m=k, n=ncols)
+    TS = lambda i: ts[str(k // 2 ** i)]  # noqa: E731
+    for d in range(1, 5):
+        got = pol.comp_plan(dict(base, driver=1, nb=64, depth=d))
+        want = models.recursive_comp(d, TS, lambda j: gemm[f"{k // 2 ** (j + 1)},{k // 2 ** (j + 1)}"])
+        assert got == pytest.approx(want, rel=1e-12)
+    for nb in (16, 64, 256):
+        i = {16: 6, 64: 4, 256: 2}[nb]  # r(i) = 2^i = k / nb
+        got = pol.comp_plan(dict(base, driver=2, nb=nb, depth=0))
+        want = models.iterative_comp(i, lambda i_: ts[str(nb)], lambda i_, j: gemm[f"{nb},{(j + 1) * nb}"])
+        assert got == pytest.approx(want, rel=1e-12)
+        got = pol.comp_plan(dict(base, driver=0, nb=nb, depth=0))
+        want = models.blocked_comp(i, lambda i_: ts[str(nb)], lambda i_: gemm[f"{nb},{nb}"])
+        assert got == pytest.approx(want, rel=1e-12)
