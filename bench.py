@@ -455,7 +455,9 @@ def run_extras(stream, rank):
       * mixed BF16 and FP8 at m = 32768, n = 4096, with plain FP64 beside them;
       * plain FP64 at m = n = 8192 in all 16 side/uplo/trans/diag forms and at
         m = n = 16384 in two more forms (Right/Upper/T/Unit, Left/Upper/T/NonUnit),
-        alpha = 1.5.
+        alpha = 1.5;
+      * the Cholesky factorisation on this TRSM, FP64, n = 16384;
+      * the 4096-instance uneven batch in FP64 and FP32 (tile autotuned).
     Inputs come from the seeded device generator (same distributions as the
     headline's); accuracy is checked on sampled columns (rows for side Right)
     against the CPU oracle."""
@@ -535,6 +537,30 @@ def run_extras(stream, rank):
     plain_leg("plain_fp64_16384_s0u1t1d0", 0, 1, 1, 0, A, B0)
     del A, B0
     torch.cuda.empty_cache()
+    # Cholesky on this TRSM (FP64, lower, n = 16384): n^3/3 flops per factorisation
+    nc = 16384
+    S0 = inputs.make_spd_device(nc, seed=5)
+    S = torch.empty_like(S0)
+    reset = lambda: S.copy_(S0)  # noqa: E731
+    infos = []
+    t, _ = _time_calls(lambda: infos.append(api.potrf(0, S, stream=stream)), reset, 1, 1, stream)
+    err = None
+    if rank == 0:
+        cols = [0, nc // 2, nc - 1]
+        L = torch.tril(S).cpu().numpy()
+        R = L @ L[cols, :].T
+        Acols = S0[:, cols].cpu().numpy()
+        err = float(np.linalg.norm(R - Acols) / np.linalg.norm(Acols))
+    for dt, nm in ((0, "batched_fp64_4096uneven"), (1, "batched_fp32_4096uneven")):
+        r = batched_measure(dt, 4096, 3, 3, stream)
+        r.pop("cpu_baseline", None)
+        out[nm] = r
+    out["potrf_fp64_16384"] = {"workload": "Cholesky A = L L^T (gb_dpotrf, lower), n = 16384, FP64, symmetric "
+                                           "diagonally dominant SPD (device generator seed 5)",
+                               "ms_per_step": t, "tflops": float(nc) ** 3 / 3 / (t * 1e-3) / 1e12,
+                               "info": infos[-1], "backward_err_sampled_cols": err}
+    del S0, S
+    torch.cuda.empty_cache()
     return out
 
 
@@ -549,25 +575,21 @@ RESIDUAL_DRAM_BYTES = {(16384, 16384, "bf16"): 19.18e9}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def run_batched(args):
-    """The uneven batch: `count` problems, m log-uniform in [16, 512], n in
-    [1, 256], side/uplo uniform (seeded), one plan (work queue + CUDA graph)
-    replayed per step; all A in one device pool, all B in another, so the
-    per-step reset of B is a single copy outside the timed events."""
+def batched_measure(dtype, count, steps, warmup, stream, cpu_baseline_on=False):
+    """The uneven batch on the current GPU: `count` problems, m log-uniform
+    in [16, 512], n in [1, 256], side/uplo uniform (seeded); the kernel's tile
+    shape picked by the library's autotuner (untimed), then one plan (work
+    queue + CUDA graph) replayed per step; all A in one device pool, all B in
+    another, so the per-step reset of B is a single copy outside the timed
+    events.  Returns a dict of the measurements."""
     import torch
 
+    import oracle
     from paper_2305_19917_gb300 import api, inputs
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local if world > 1 else 0)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    dev = torch.cuda.current_device()
-    api.lib()
-    dt = 0 if args.dtype == "f64" else 1
+    dt = dtype
     tdt = torch.float64 if dt == 0 else torch.float32
-    items = inputs.make_batch(args.count, seed=0)
+    items = inputs.make_batch(count, seed=0)
     a_sizes = [it["A"].size for it in items]
     b_sizes = [it["B"].size for it in items]
     Apool = torch.empty(int(sum(a_sizes)) + 16, dtype=tdt, device="cuda")
@@ -584,12 +606,11 @@ def run_batched(args):
         oa += sa
         ob += sb
     B0 = Bpool.clone()
-    stream = torch.cuda.current_stream()
-    plan = api.BatchedPlan(dt, descs, stream.cuda_stream)
+    tile, tile_ms = api.gb_batched_autotune(dt, descs, reps=3, stream=stream.cuda_stream)
+    plan = api.BatchedPlan(dt, descs, stream.cuda_stream, tile=tile)
     info = plan.info()
     flops = info["flops"]
     esz = Apool.element_size()
-    alg_bytes = esz * sum(0.5 * it["A"].shape[0] ** 2 + 2 * it["B"].size for it in items)
 
     def reset():
         Bpool.copy_(B0)
@@ -597,26 +618,17 @@ def run_batched(args):
     def solve():
         plan.run(stream.cuda_stream)
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         reset()
         solve()
     torch.cuda.synchronize()
-    clocks = ClockSampler(dev)
-    clocks.start()
     api.gb_profile_enable(1)
     l0 = api.gb_kernel_launches()
-    ms, _ = _timed_steps(solve, reset, args.steps, stream)
+    ms, _ = _timed_steps(solve, reset, steps, stream)
     launches = api.gb_kernel_launches() - l0
-    clk = clocks.stop()
     prof = api.gb_profile_read(api.KERNEL_KINDS.index("batched"))
     api.gb_profile_enable(0)
     ms_step = float(np.mean(ms))
-    if world > 1:
-        from paper_2305_19917_gb300 import dist as gdist
-        ms_step = gdist.max_over_ranks(ms_step, device="cuda")
-    value = world * flops / (ms_step * 1e-3) / 1e12
-    # accuracy on sampled instances
-    import oracle
     errs = []
     for idx in range(0, len(items), max(1, len(items) // 32)):
         it = items[idx]
@@ -642,7 +654,7 @@ def run_batched(args):
     achieved = prof["flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] > 0 else 0.0
     hbm = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else 0.0
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if cpu_baseline_on:
         t0 = time.perf_counter()
         sample = items[: max(1, len(items) // 16)]
         fl = 0.0
@@ -653,29 +665,60 @@ def run_batched(args):
         dtc = time.perf_counter() - t0
         cpu = {"value": fl / dtc / 1e12, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
                "sample": f"first {len(sample)} of the {len(items)} problems, FP64 oracle, {dtc:.1f} s"}
+    out = {"workload": f"batched uneven TRSM ({'FP64' if dt == 0 else 'FP32'}): {len(items)} problems, m log-uniform "
+                       f"[16,512], n uniform [1,256], side/uplo uniform, seed 0; one persistent launch (device work "
+                       f"queue, CUDA graph)",
+           "ms_per_step": ms_step, "tflops": flops / (ms_step * 1e-3) / 1e12, "units": info["units"],
+           "grid": info["grid"], "tile": tile, "tile_autotune_ms": tile_ms, "launches": int(launches),
+           "roofline": {"kernel": "batched", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_source": "derived from SM count x FMA units x 2.07 GHz",
+                        "hbm_gbs": hbm, "hbm_frac": hbm / MEASURED_PEAKS.get("hbm_gbs", 6797.2),
+                        "launches": prof["launches"], "ms_total": prof["ms"]},
+           "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+                   "h2d_bytes_per_step": int((Apool.numel() + Bpool.numel()) * esz),
+                   "d2h_bytes_per_step": int(Bpool.numel() * esz)},
+           "cpu_baseline": cpu, "fwd_err_max_sampled": max(errs), "instances_checked": len(errs),
+           "pool_mb": (Apool.numel() + Bpool.numel()) * esz / 1e6}
+    plan.close()
+    return out
+
+
+def run_batched(args):
+    """--path batched: the uneven batch as the timed step."""
+    import torch
+
+    from paper_2305_19917_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local if world > 1 else 0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    api.lib()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    r = batched_measure(0 if args.dtype == "f64" else 1, args.count, args.steps, args.warmup, stream,
+                        cpu_baseline_on=(not args.no_cpu_baseline and world == 1))
+    clk = clocks.stop()
+    ms_step = r["ms_per_step"]
+    if world > 1:
+        from paper_2305_19917_gb300 import dist as gdist
+        ms_step = gdist.max_over_ranks(ms_step, device="cuda")
+    value = world * r["tflops"] * r["ms_per_step"] / ms_step
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-                "config": {"workload": f"batched uneven TRSM: {len(items)} problems, m log-uniform [16,512], "
-                                       f"n uniform [1,256], side/uplo uniform, seed 0; one persistent launch "
-                                       f"(device work queue, CUDA graph)",
-                           "units": info["units"], "grid": info["grid"],
-                           "l2": "B reset by one copy before each step; A+B pools exceed L2 "
-                                 f"({(Apool.numel() + Bpool.numel()) * esz / 1e6:.0f} MB)"},
-                "roofline": {"kernel": "batched", "bound": "alu", "achieved": achieved, "peak": peak,
-                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                             "peak_source": "derived from SM count x FMA units x 2.07 GHz",
-                             "hbm_gbs": hbm, "hbm_frac": hbm / MEASURED_PEAKS.get("hbm_gbs", 6797.2),
-                             "launches": prof["launches"], "ms_total": prof["ms"]},
-                "cpu_baseline": cpu,
-                "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
-                        "h2d_bytes_per_step": int((Apool.numel() + Bpool.numel()) * esz),
-                        "d2h_bytes_per_step": int(Bpool.numel() * esz)},
-                "gpu_launches": int(launches), "clocks": clk,
-                "accuracy": {"fwd_err_max_sampled": max(errs), "instances_checked": len(errs)}}
+                "config": {"workload": r["workload"], "units": r["units"], "grid": r["grid"], "tile": r["tile"],
+                           "l2": f"B reset by one copy before each step; A+B pools exceed L2 ({r['pool_mb']:.0f} MB)"},
+                "roofline": r["roofline"], "cpu_baseline": r["cpu_baseline"], "e2e": r["e2e"],
+                "gpu_launches": r["launches"], "clocks": clk,
+                "accuracy": {"fwd_err_max_sampled": r["fwd_err_max_sampled"],
+                             "instances_checked": r["instances_checked"]}}
         print(json.dumps(line), flush=True)
-    plan.close()
     return 0
 
 

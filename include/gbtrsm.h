@@ -334,7 +334,8 @@ int gb_mixed_history(double *rho, int *levels, int cap);
  * A negative status -a names the argument a whose entry is invalid (or
  * whose array is NULL).  Problems of order (m for Left, n for Right) up to
  * 512 are solved in shared memory by the persistent kernel, in chunks of 16
- * (FP64) or 32 (FP32) right-hand sides, largest first; larger problems are
+ * (FP64) or 32 (FP32) right-hand sides (the default tile; see
+ * gb_batched_plan_create_tiled), largest first; larger problems are
  * solved one after the other by the regular driver on the same stream.
  * Synchronous (returns after the solves completed).
  *
@@ -359,6 +360,40 @@ int gb_batched_plan_create(int dtype, int64_t count, const int8_t *side,
                            const void *const *A, const int64_t *lda,
                            void *const *B, const int64_t *ldb, void *stream,
                            void **plan_out);
+/*
+ * gb_batched_plan_create_tiled: as gb_batched_plan_create with the tile
+ * shape of the kernel's gemm tasks as argument 14 (stream 15, plan_out 16):
+ * tile = rows of a 32-row block row per thread, 1 (units of 16 FP64 / 32
+ * FP32 right-hand sides, several CTAs per SM) or 2 (units of 32 / 64
+ * right-hand sides, twice the multiply-adds per shared-memory load, one CTA
+ * per SM); 0 = 1.  Any other value returns -15; a NULL plan_out -17.
+ * gb_batched_plan_create is this with tile 1.
+ * gb_batched_plan_tile(plan): the plan's tile (or -1 for NULL).
+ *
+ * gb_batched_autotune(... 1-13 as gb_trsm_batched ..., int reps, stream,
+ *   int *tile_out, double *ms_out): the autotuner of the batched kernel's
+ *   tile shape: builds a plan with each tile, times `reps` replays of each
+ *   (after one warm-up; CUDA events, median) with every B restored from a
+ *   device copy before each replay, and returns the fastest tile in
+ *   *tile_out and the two medians in ms_out[0..1] (optional).  B is left as
+ *   it was.  Synchronous; its copy of the B's comes from the stream-ordered
+ *   allocator.  Returns 0, -14 for reps outside 1..100, -16 for a NULL
+ *   tile_out, or a plan-creation / CUDA status.
+ */
+int gb_batched_plan_create_tiled(int dtype, int64_t count, const int8_t *side,
+                                 const int8_t *uplo, const int8_t *trans,
+                                 const int8_t *diag, const int64_t *m,
+                                 const int64_t *n, const void *alpha,
+                                 const void *const *A, const int64_t *lda,
+                                 void *const *B, const int64_t *ldb, int tile,
+                                 void *stream, void **plan_out);
+int gb_batched_plan_tile(const void *plan);
+int gb_batched_autotune(int dtype, int64_t count, const int8_t *side,
+                        const int8_t *uplo, const int8_t *trans,
+                        const int8_t *diag, const int64_t *m, const int64_t *n,
+                        const void *alpha, const void *const *A,
+                        const int64_t *lda, void *const *B, const int64_t *ldb,
+                        int reps, void *stream, int *tile_out, double *ms_out);
 int gb_batched_plan_run(void *plan, void *stream);
 int gb_batched_plan_destroy(void *plan);
 int gb_batched_plan_info(const void *plan, int64_t *units, int *grid,

@@ -67,6 +67,11 @@ _SIGS = {
     "gb_trsm_batched": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "gb_batched_plan_create": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                 ctypes.POINTER(vp)], i32),
+    "gb_batched_plan_create_tiled": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp,
+                                      ctypes.POINTER(vp)], i32),
+    "gb_batched_autotune": ([i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, ctypes.POINTER(i32),
+                             ctypes.POINTER(dbl)], i32),
+    "gb_batched_plan_tile": ([vp], i32),
     "gb_batched_plan_run": ([vp, vp], i32),
     "gb_batched_plan_destroy": ([vp], i32),
     "gb_batched_plan_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
@@ -283,16 +288,29 @@ def gb_trsm_batched(dtype, items, stream=0):
     return lib().gb_trsm_batched(dtype, *a.args(), stream or None)
 
 
-class BatchedPlan:
-    """gb_batched_plan_* handle (work queue + CUDA graph for fixed pointers)."""
+def gb_batched_autotune(dtype, items, reps=3, stream=0):
+    """Time the batched kernel's tile shapes on these problems (B restored
+    afterwards).  Returns (best tile, [ms with tile 1, ms with tile 2])."""
+    a = _BatchArgs(dtype, items)
+    tile, ms = i32(), (dbl * 2)()
+    st = lib().gb_batched_autotune(dtype, *a.args(), reps, stream or None, ctypes.byref(tile), ms)
+    if st != 0:
+        raise GbError("gb_batched_autotune", st)
+    return tile.value, [ms[0], ms[1]]
 
-    def __init__(self, dtype, items, stream=0):
+
+class BatchedPlan:
+    """gb_batched_plan_* handle (work queue + CUDA graph for fixed pointers);
+    tile = rows per thread of the kernel's gemm tasks (1 or 2; 0 = default)."""
+
+    def __init__(self, dtype, items, stream=0, tile=0):
         self._args = _BatchArgs(dtype, items)
         h = vp()
-        st = lib().gb_batched_plan_create(dtype, *self._args.args(), stream or None, ctypes.byref(h))
+        st = lib().gb_batched_plan_create_tiled(dtype, *self._args.args(), tile, stream or None, ctypes.byref(h))
         if st != 0:
-            raise GbError("gb_batched_plan_create", st)
+            raise GbError("gb_batched_plan_create_tiled", st)
         self.handle = h
+        self.tile = lib().gb_batched_plan_tile(h)
 
     def run(self, stream=0):
         st = lib().gb_batched_plan_run(self.handle, stream or None)

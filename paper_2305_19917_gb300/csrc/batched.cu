@@ -13,6 +13,14 @@
 // by warp-shuffle substitution (the TS task).  Backward problems are index
 // reversed and right-side problems transposed on the way in and out.
 // Instances of order above KMAX are solved by the regular driver.
+//
+// Tile shapes (the autotuner's choice, gb_batched_autotune): in the gemm
+// tasks each thread owns RR rows x one 16-byte vector of right-hand sides
+// (PER = 2 FP64 / 4 FP32 columns), so a unit is CW = 8 PER RR right-hand
+// sides wide: RR = 1 gives 16 (FP64) / 32 (FP32) columns and three CTAs per
+// SM; RR = 2 gives 32 / 64 columns, twice the multiply-adds per shared-memory
+// load, one CTA per SM.  A tiles are stored k-major so that a thread's RR
+// rows load as one vector.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -25,16 +33,18 @@ namespace {
 constexpr int KMAX = 512;   // largest order solved in shared memory
 constexpr int NBB = 32;     // diagonal block
 constexpr int NT = 256;     // threads per CTA
+constexpr int LT = NBB + 2; // k-major A tile: row stride of one k (keeps 8- and 16-byte alignment)
 
-template <typename T>
-struct BCfg;
-template <>
-struct BCfg<double> {
-    static constexpr int CW = 16;  // right-hand sides per unit
-};
-template <>
-struct BCfg<float> {
-    static constexpr int CW = 32;
+// Tile shape of the gemm tasks: RR rows x PER columns per thread.
+template <typename T, int RR>
+struct BCfg {
+    static constexpr int PER = int(16 / sizeof(T));   // one 16-byte vector of right-hand sides
+    static constexpr int ROWG = NBB / RR;             // row groups of a block row
+    static constexpr int COLG = NT / ROWG;            // column groups
+    static constexpr int CW = COLG * PER;             // right-hand sides per unit
+    static constexpr int LX = CW + PER;               // row stride of X in shared memory
+    static_assert(ROWG * COLG == NT, "thread split");
+    static_assert(CW % 8 == 0, "warp split of the TS task");
 };
 
 template <typename T>
@@ -89,7 +99,8 @@ __device__ __forceinline__ void tile_of(int t, int &jb, int &ib)
 
 // Issue the asynchronous loads of tile t into buffer Tb (reading along A's
 // contiguous dimension): the gemm tiles in full, the TS tile on and below
-// its diagonal; everything else (and the ragged edge) reads as zero.
+// its diagonal; everything else (and the ragged edge) reads as zero.  Tb is
+// k-major: Tb[kk * LT + rr] = Mv'(j0 + rr, i0 + kk).
 template <typename T>
 __device__ __forceinline__ void load_tile(const Unit<T> &u, int t, T *Tb)
 {
@@ -101,23 +112,43 @@ __device__ __forceinline__ void load_tile(const Unit<T> &u, int t, T *Tb)
         const int fast = idx % NBB, slow = idx / NBB;
         const int rr = mt ? slow : fast, kk = mt ? fast : slow;
         const bool in = j0 + rr < k && i0 + kk < k && (ib < jb || kk <= rr);
-        cp_async_elem(Tb + rr * (NBB + 1) + kk, in ? mv_addr(u, j0 + rr, i0 + kk) : u.A, in);
+        cp_async_elem(Tb + kk * LT + rr, in ? mv_addr(u, j0 + rr, i0 + kk) : u.A, in);
     }
 }
 
-// smem: Xs[KMAX][LX], NBUF tiles Ts[NBB][NBB+1], inverse diagonal.
-template <typename T>
+// RR rows of a k-major A tile as one vector.
+template <typename T, int RR>
+struct RowVec {
+    T v[RR];
+};
+template <typename T, int RR>
+__device__ __forceinline__ void load_rows(const T *p, T (&a)[RR])
+{
+    if constexpr (RR * sizeof(T) == 16) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(p);
+        const T *x = reinterpret_cast<const T *>(&q);
+#pragma unroll
+        for (int e = 0; e < RR; e++) a[e] = x[e];
+    } else if constexpr (RR * sizeof(T) == 8) {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        const T *x = reinterpret_cast<const T *>(&q);
+#pragma unroll
+        for (int e = 0; e < RR; e++) a[e] = x[e];
+    } else {
+#pragma unroll
+        for (int e = 0; e < RR; e++) a[e] = p[e];
+    }
+}
+
+// smem: Xs[KMAX][LX], NBUF k-major tiles Ts[NBB][LT], inverse diagonal.
+template <typename T, int RR>
 __global__ void __launch_bounds__(NT)
 batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restrict__ ticket)
 {
-    constexpr int CW = BCfg<T>::CW;
-    // row stride of Xs: padded to 16 bytes so that a thread's PER columns
-    // load as one vector (every thread of a warp reads the same row: a
-    // broadcast)
-    constexpr int LX = CW + int(16 / sizeof(T));
-    constexpr int PER = CW / 8;  // outputs per thread in the update (8 threads per row)
-    static_assert(PER * sizeof(T) == 16, "one 16-byte vector of X per thread and k");
-    constexpr int TS = NBB * (NBB + 1);
+    using C = BCfg<T, RR>;
+    constexpr int CW = C::CW, LX = C::LX, PER = C::PER;
+    constexpr int TS = NBB * LT;
+    constexpr int CPW = CW / 8;  // columns per warp in the TS task
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);
     T *Ts = Xs + KMAX * LX;
@@ -159,10 +190,12 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
             cp_async_commit();
         }
 
-        const int r = tid >> 3, cq = (tid & 7) * PER;
-        T acc[PER];
+        const int r = (tid / C::COLG) * RR, cq = (tid % C::COLG) * PER;
+        T acc[RR][PER];
 #pragma unroll
-        for (int e = 0; e < PER; e++) acc[e] = T(0);
+        for (int a = 0; a < RR; a++)
+#pragma unroll
+            for (int e = 0; e < PER; e++) acc[a][e] = T(0);
         for (int tt = 0; tt < ntile; tt++) {
             // keep NBUF - 1 tiles in flight: issue tile tt + NBUF - 1, then
             // wait until tile tt (and the B chunk) has landed
@@ -179,32 +212,38 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
                 const int i0 = ib * NBB;
 #pragma unroll 8
                 for (int kk = 0; kk < NBB; kk++) {
-                    const T a = Tb[r * (NBB + 1) + kk];
+                    T a[RR];
+                    load_rows<T, RR>(Tb + kk * LT + r, a);
                     const uint4 xv = *reinterpret_cast<const uint4 *>(Xs + (i0 + kk) * LX + cq);
                     const T *x = reinterpret_cast<const T *>(&xv);
 #pragma unroll
-                    for (int e = 0; e < PER; e++) acc[e] += a * x[e];
+                    for (int q = 0; q < RR; q++)
+#pragma unroll
+                        for (int e = 0; e < PER; e++) acc[q][e] += a[q] * x[e];
                 }
             } else {
                 // X_j -= sum of the gemm tasks, then the TS task: the nr x nr
                 // triangle by warp-shuffle substitution
-                if (r < nr) {
 #pragma unroll
-                    for (int e = 0; e < PER; e++) Xs[(j0 + r) * LX + cq + e] -= acc[e];
+                for (int q = 0; q < RR; q++) {
+                    if (r + q < nr) {
+#pragma unroll
+                        for (int e = 0; e < PER; e++) Xs[(j0 + r + q) * LX + cq + e] -= acc[q][e];
+                    }
+#pragma unroll
+                    for (int e = 0; e < PER; e++) acc[q][e] = T(0);
                 }
-#pragma unroll
-                for (int e = 0; e < PER; e++) acc[e] = T(0);
-                if (tid < NBB) inv[tid] = (tid < nr && !unitd) ? T(1) / Tb[tid * (NBB + 1) + tid] : T(1);
+                if (tid < NBB) inv[tid] = (tid < nr && !unitd) ? T(1) / Tb[tid * LT + tid] : T(1);
                 __syncthreads();
-                // warp w solves columns w, w+8, ... (PER columns, interleaved for ILP)
-                T tv[PER];
+                // warp w solves columns w, w+8, ... (CPW columns, interleaved for ILP)
+                T tv[CPW];
 #pragma unroll
-                for (int e = 0; e < PER; e++) tv[e] = (lane < nr) ? Xs[(j0 + lane) * LX + warp + 8 * e] : T(0);
+                for (int e = 0; e < CPW; e++) tv[e] = (lane < nr) ? Xs[(j0 + lane) * LX + warp + 8 * e] : T(0);
                 for (int kk = 0; kk < nr; kk++) {
                     const T d = inv[kk];
-                    const T lk = Tb[lane * (NBB + 1) + kk];
+                    const T lk = Tb[kk * LT + lane];
 #pragma unroll
-                    for (int e = 0; e < PER; e++) {
+                    for (int e = 0; e < CPW; e++) {
                         const T x = __shfl_sync(0xffffffffu, tv[e], kk) * d;
                         if (lane == kk) tv[e] = x;
                         else if (lane > kk) tv[e] -= lk * x;
@@ -212,7 +251,7 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
                 }
                 if (lane < nr) {
 #pragma unroll
-                    for (int e = 0; e < PER; e++) Xs[(j0 + lane) * LX + warp + 8 * e] = tv[e];
+                    for (int e = 0; e < CPW; e++) Xs[(j0 + lane) * LX + warp + 8 * e] = tv[e];
                 }
             }
             __syncthreads();  // the buffer of tile tt is reused NBUF - 1 tiles later
@@ -235,10 +274,10 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
     }
 }
 
-template <typename T>
+template <typename T, int RR>
 constexpr size_t batched_smem()
 {
-    return sizeof(T) * (size_t(KMAX) * (BCfg<T>::CW + 16 / sizeof(T)) + NBUF * NBB * (NBB + 1) + NBB);
+    return sizeof(T) * (size_t(KMAX) * BCfg<T, RR>::LX + NBUF * NBB * LT + NBB);
 }
 
 }  // namespace
@@ -247,6 +286,7 @@ constexpr size_t batched_smem()
 
 struct BatchedPlan {
     int dtype = 0;                 // 0 FP64, 1 FP32
+    int tile = 1;                  // rows per thread in the gemm tasks (1 or 2)
     int64_t nunits = 0;
     void *units = nullptr;         // device array of Unit<T>
     unsigned *ticket = nullptr;    // device work-queue counter
@@ -272,7 +312,7 @@ void build_units(BatchedPlan &P, int64_t count, const int8_t *side, const int8_t
                  const int8_t *diag, const int64_t *m, const int64_t *n, const T *alpha, const void *const *A,
                  const int64_t *lda, void *const *B, const int64_t *ldb, std::vector<Unit<T>> &units)
 {
-    constexpr int CW = BCfg<T>::CW;
+    const int CW = P.tile == 2 ? BCfg<T, 2>::CW : BCfg<T, 1>::CW;
     for (int64_t i = 0; i < count; i++) {
         if (m[i] == 0 || n[i] == 0) continue;
         const bool left = side[i] == GB_LEFT;
@@ -307,7 +347,7 @@ void build_units(BatchedPlan &P, int64_t count, const int8_t *side, const int8_t
                      [](const Unit<T> &a, const Unit<T> &b) { return a.k * a.cw > b.k * b.cw; });
 }
 
-template <typename T>
+template <typename T, int RR>
 int upload_and_capture(BatchedPlan &P, std::vector<Unit<T>> &units, cudaStream_t s)
 {
     P.nunits = int64_t(units.size());
@@ -317,11 +357,11 @@ int upload_and_capture(BatchedPlan &P, std::vector<Unit<T>> &units, cudaStream_t
     if (ub) GB_CUDA(cudaMemcpyAsync(P.units, units.data(), ub, cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaStreamSynchronize(s));
     static PerDeviceOnce attr;
-    GB_TRY(smem_attr_once(attr, batched_kernel<T>, batched_smem<T>()));
+    GB_TRY(smem_attr_once(attr, batched_kernel<T, RR>, batched_smem<T, RR>()));
     int dev = 0, sms = 0, per_sm = 0;
     GB_CUDA(cudaGetDevice(&dev));
     GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T>, NT, batched_smem<T>()));
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T, RR>, NT, batched_smem<T, RR>()));
     if (per_sm < 1) per_sm = 1;
     int64_t g = int64_t(sms) * per_sm;
     if (g > P.nunits) g = P.nunits;
@@ -336,8 +376,8 @@ int upload_and_capture(BatchedPlan &P, std::vector<Unit<T>> &units, cudaStream_t
         cudaMemsetAsync(P.ticket, 0, sizeof(unsigned), cs);
         {
             LaunchScope ls(KK_BATCHED, cs, P.flops, P.bytes);
-            batched_kernel<T><<<P.grid, NT, batched_smem<T>(), cs>>>(static_cast<const Unit<T> *>(P.units),
-                                                                     int(P.nunits), P.ticket);
+            batched_kernel<T, RR><<<P.grid, NT, batched_smem<T, RR>(), cs>>>(
+                static_cast<const Unit<T> *>(P.units), int(P.nunits), P.ticket);
         }
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cs, &graph);
@@ -383,7 +423,7 @@ void batched_free(BatchedPlan *P)
 
 int batched_create(int dtype, int64_t count, const int8_t *side, const int8_t *uplo, const int8_t *trans,
                    const int8_t *diag, const int64_t *m, const int64_t *n, const void *alpha, const void *const *A,
-                   const int64_t *lda, void *const *B, const int64_t *ldb, cudaStream_t s, BatchedPlan **out)
+                   const int64_t *lda, void *const *B, const int64_t *ldb, cudaStream_t s, int tile, BatchedPlan **out)
 {
     // argument checks (1-based argument numbers of gb_trsm_batched)
     if (dtype != 0 && dtype != 1) return -1;
@@ -410,17 +450,18 @@ int batched_create(int dtype, int64_t count, const int8_t *side, const int8_t *u
     }
     BatchedPlan *P = new BatchedPlan;
     P->dtype = dtype;
+    P->tile = tile;
     int st;
     if (dtype == 0) {
         std::vector<Unit<double>> units;
         build_units<double>(*P, count, side, uplo, trans, diag, m, n, static_cast<const double *>(alpha), A, lda, B,
                             ldb, units);
-        st = upload_and_capture<double>(*P, units, s);
+        st = tile == 2 ? upload_and_capture<double, 2>(*P, units, s) : upload_and_capture<double, 1>(*P, units, s);
     } else {
         std::vector<Unit<float>> units;
         build_units<float>(*P, count, side, uplo, trans, diag, m, n, static_cast<const float *>(alpha), A, lda, B,
                            ldb, units);
-        st = upload_and_capture<float>(*P, units, s);
+        st = tile == 2 ? upload_and_capture<float, 2>(*P, units, s) : upload_and_capture<float, 1>(*P, units, s);
     }
     if (st) {
         batched_free(P);
@@ -434,19 +475,113 @@ int batched_create(int dtype, int64_t count, const int8_t *side, const int8_t *u
 
 extern "C" {
 
+int gb_batched_plan_create_tiled(int dtype, int64_t count, const int8_t *side, const int8_t *uplo,
+                                 const int8_t *trans, const int8_t *diag, const int64_t *m, const int64_t *n,
+                                 const void *alpha, const void *const *A, const int64_t *lda, void *const *B,
+                                 const int64_t *ldb, int tile, void *stream, void **plan_out)
+{
+    if (!plan_out) return -17;
+    *plan_out = nullptr;
+    if (tile == 0) tile = 1;
+    if (tile != 1 && tile != 2) return -15;
+    gb::BatchedPlan *P = nullptr;
+    int st = gb::batched_create(dtype, count, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb,
+                                static_cast<cudaStream_t>(stream), tile, &P);
+    if (st) return st;
+    *plan_out = P;
+    return 0;
+}
+
 int gb_batched_plan_create(int dtype, int64_t count, const int8_t *side, const int8_t *uplo, const int8_t *trans,
                            const int8_t *diag, const int64_t *m, const int64_t *n, const void *alpha,
                            const void *const *A, const int64_t *lda, void *const *B, const int64_t *ldb,
                            void *stream, void **plan_out)
 {
     if (!plan_out) return -15;
-    *plan_out = nullptr;
-    gb::BatchedPlan *P = nullptr;
-    int st = gb::batched_create(dtype, count, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb,
-                                static_cast<cudaStream_t>(stream), &P);
-    if (st) return st;
-    *plan_out = P;
-    return 0;
+    const int st = gb_batched_plan_create_tiled(dtype, count, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb,
+                                                1, stream, plan_out);
+    return st == -17 ? -15 : st;
+}
+
+int gb_batched_autotune(int dtype, int64_t count, const int8_t *side, const int8_t *uplo, const int8_t *trans,
+                        const int8_t *diag, const int64_t *m, const int64_t *n, const void *alpha,
+                        const void *const *A, const int64_t *lda, void *const *B, const int64_t *ldb, int reps,
+                        void *stream, int *tile_out, double *ms_out)
+{
+    if (!tile_out) return -16;
+    if (reps < 1 || reps > 100) return -14;
+    *tile_out = 1;
+    if (ms_out) ms_out[0] = ms_out[1] = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the solves overwrite B: keep a device copy of every B and restore it
+    // before each run and at the end
+    const size_t esz = dtype == 0 ? 8 : 4;
+    std::vector<size_t> off(count > 0 ? size_t(count) : 1, 0);
+    size_t total = 0;
+    for (int64_t i = 0; i < count; i++) {
+        off[i] = total;
+        if (m && n && m[i] > 0 && n[i] > 0) total += size_t(m[i]) * size_t(n[i]) * esz;
+    }
+    void *save = nullptr;
+    if (total) GB_CUDA(cudaMallocAsync(&save, total, s));
+    auto copy_all = [&](bool restore) {
+        for (int64_t i = 0; i < count; i++) {
+            if (m[i] <= 0 || n[i] <= 0) continue;
+            char *sv = static_cast<char *>(save) + off[i];
+            const cudaError_t e =
+                restore ? cudaMemcpy2DAsync(B[i], esz * ldb[i], sv, esz * m[i], esz * m[i], n[i], cudaMemcpyDeviceToDevice, s)
+                        : cudaMemcpy2DAsync(sv, esz * m[i], B[i], esz * ldb[i], esz * m[i], n[i], cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return gb::check(e);
+        }
+        return 0;
+    };
+    int st = 0;
+    double best = 1e300;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!st) st = gb::check(cudaEventCreate(&e0));
+    if (!st) st = gb::check(cudaEventCreate(&e1));
+    if (!st && total) st = copy_all(false);
+    for (int tile = 1; tile <= 2 && !st; tile++) {
+        void *plan = nullptr;
+        st = gb_batched_plan_create_tiled(dtype, count, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, tile,
+                                          stream, &plan);
+        if (st) break;
+        std::vector<float> t(reps);
+        for (int r = 0; r <= reps && !st; r++) {  // run 0 is a warm-up
+            if (total) st = copy_all(true);
+            if (st) break;
+            cudaEventRecord(e0, s);
+            st = gb_batched_plan_run(plan, stream);
+            cudaEventRecord(e1, s);
+            if (!st) st = gb::check(cudaEventSynchronize(e1));
+            if (!st && r > 0) st = gb::check(cudaEventElapsedTime(&t[r - 1], e0, e1));
+        }
+        gb_batched_plan_destroy(plan);
+        if (st) break;
+        std::sort(t.begin(), t.end());
+        const double ms = t[reps / 2];
+        if (ms_out) ms_out[tile - 1] = ms;
+        if (ms < best) {
+            best = ms;
+            *tile_out = tile;
+        }
+    }
+    if (total && save) {
+        const int c = copy_all(true);
+        if (!st) st = c;
+        cudaFreeAsync(save, s);
+    }
+    const int c = gb::check(cudaStreamSynchronize(s));
+    if (!st) st = c;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return st;
+}
+
+int gb_batched_plan_tile(const void *plan)
+{
+    if (!plan) return -1;
+    return static_cast<const gb::BatchedPlan *>(plan)->tile;
 }
 
 int gb_batched_plan_run(void *plan, void *stream)

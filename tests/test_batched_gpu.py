@@ -66,6 +66,40 @@ def test_batched_mixed_forms_and_sizes(dtype):
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("tile", [1, 2])
+def test_batched_tiles_mixed_forms(dtype, tile):
+    """Both tile shapes of the batched kernel (units of 8 PER tile right-hand
+    sides) on the mixed forms, ragged sizes and two large instances."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    items = _random_items(40, seed=11 + dtype + 2 * tile, nmax=150, big=(5,))
+    keep, descs = _device_batch(items, dtype)
+    plan = api.BatchedPlan(dtype, descs, tile=tile)
+    assert plan.tile == tile
+    plan.run(torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    plan.close()
+    for it, (Ad, Bd) in zip(items, keep):
+        X = Bd.double().cpu().numpy()
+        Xo = oracle.dtrsm(it["side"], it["uplo"], it["trans"], it["diag"], it["alpha"], it["A"], it["B"])
+        assert fwd_err(X, Xo) <= TOL[dtype], (tile, it["side"], it["uplo"], it["trans"], it["diag"], it["B"].shape)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_batched_autotune_restores_b_and_picks_a_tile(dtype):
+    import torch
+    from paper_2305_19917_gb300 import api
+    items = inputs.make_batch(300, seed=13)
+    keep, descs = _device_batch(items, dtype)
+    before = [Bd.clone() for _, Bd in keep]
+    tile, ms = api.gb_batched_autotune(dtype, descs, reps=2, stream=torch.cuda.current_stream().cuda_stream)
+    assert tile in (1, 2) and all(t > 0 for t in ms)
+    assert ms[tile - 1] == min(ms)
+    for (_, Bd), B0 in zip(keep, before):
+        assert torch.equal(Bd, B0)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
 def test_batched_plan_replay_and_config_recipe(dtype):
     """The 4096-instance uneven recipe (m log-uniform in [16, 512], n in
     [1, 256], side/uplo uniform); sampled instances vs the oracle after two
@@ -75,7 +109,8 @@ def test_batched_plan_replay_and_config_recipe(dtype):
     items = inputs.make_batch(4096, seed=7)
     keep, descs = _device_batch(items, dtype)
     originals = [Bd.clone() for _, Bd in keep]
-    plan = api.BatchedPlan(dtype, descs)
+    tile, _ = api.gb_batched_autotune(dtype, descs, reps=2, stream=torch.cuda.current_stream().cuda_stream)
+    plan = api.BatchedPlan(dtype, descs, tile=tile)
     info = plan.info()
     assert info["large_instances"] == 0 and info["units"] >= 4096
     for _ in range(2):
