@@ -21,6 +21,15 @@
 // SM; RR = 2 gives 32 / 64 columns, twice the multiply-adds per shared-memory
 // load, one CTA per SM.  A tiles are stored k-major so that a thread's RR
 // rows load as one vector.
+//
+// FP32 solves the 32 x 32 diagonal blocks with their inverses: a first kernel
+// of the plan's graph inverts every diagonal block of every instance once per
+// run (one warp per block, one lane per column of the inverse, forward
+// substitution in registers), and the TS task of a unit becomes a product
+// with the inverse on the gemm tasks' register tiles -- the warp-shuffle
+// substitution, about four times the instructions of a gemm tile, dominated
+// the FP32 kernel's issue slots.  FP64 keeps the substitution: its DFMA rate,
+// not instruction issue, bounds it.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -51,6 +60,7 @@ template <typename T>
 struct Unit {
     const T *A;   // A of the instance
     T *B;         // B of the instance, offset to the chunk's first right-hand side
+    const T *Linv;  // inverses of the instance's 32 x 32 diagonal blocks (FP32), k-major 32 x 32 each
     int64_t lda, ldb;
     int k;        // order of the triangle
     int cw;       // right-hand sides in this chunk (<= CW)
@@ -59,7 +69,11 @@ struct Unit {
 };
 
 
-constexpr int NBUF = 4;  // A tiles in flight per CTA
+// A tiles in the ring (NBUF - 1 in flight): the tiles stream from L2, whose
+// latency a short ring leaves exposed; FP32 tiles are half the size, so it
+// keeps twice as many.
+template <typename T>
+constexpr int nbuf() { return sizeof(T) == 4 ? 8 : 4; }
 
 // Asynchronous copy of one element (4 or 8 bytes); `in` false writes zero.
 template <typename T>
@@ -106,6 +120,18 @@ __device__ __forceinline__ void load_tile(const Unit<T> &u, int t, T *Tb)
 {
     int jb, ib;
     tile_of(t, jb, ib);
+    if (u.Linv && ib == jb) {
+        // the TS task's tile: the block's precomputed inverse (k-major 32 x
+        // 32 in global memory), in 8-byte pieces into the LT-strided layout
+        const T *src = u.Linv + size_t(jb) * NBB * NBB;
+        constexpr int PIECE = int(8 / sizeof(T));
+        for (int idx = threadIdx.x; idx < NBB * NBB / PIECE; idx += NT) {
+            const int kk = (idx * PIECE) / NBB, rr = (idx * PIECE) % NBB;
+            const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(Tb + kk * LT + rr));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src + kk * NBB + rr) : "memory");
+        }
+        return;
+    }
     const int j0 = jb * NBB, i0 = ib * NBB, k = u.k;
     const bool mt = u.flags & 1;
     for (int idx = threadIdx.x; idx < NBB * NBB; idx += NT) {
@@ -152,6 +178,7 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);
     T *Ts = Xs + KMAX * LX;
+    constexpr int NBUF = nbuf<T>();
     T *inv = Ts + NBUF * TS;
     __shared__ int cur;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -221,6 +248,40 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
 #pragma unroll
                         for (int e = 0; e < PER; e++) acc[q][e] += a[q] * x[e];
                 }
+            } else if (u.Linv) {
+                // X_j -= sum of the gemm tasks, then the TS task as the
+                // product X_j = L_jj^-1 X_j on the register tiles
+#pragma unroll
+                for (int q = 0; q < RR; q++) {
+                    if (r + q < nr) {
+#pragma unroll
+                        for (int e = 0; e < PER; e++) Xs[(j0 + r + q) * LX + cq + e] -= acc[q][e];
+                    }
+#pragma unroll
+                    for (int e = 0; e < PER; e++) acc[q][e] = T(0);
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int kk = 0; kk < NBB; kk++) {
+                    T a[RR];
+                    load_rows<T, RR>(Tb + kk * LT + r, a);
+                    const uint4 xv = *reinterpret_cast<const uint4 *>(Xs + (j0 + kk) * LX + cq);
+                    const T *x = reinterpret_cast<const T *>(&xv);
+#pragma unroll
+                    for (int q = 0; q < RR; q++)
+#pragma unroll
+                        for (int e = 0; e < PER; e++) acc[q][e] += a[q] * x[e];
+                }
+                __syncthreads();  // every thread has read X_j
+#pragma unroll
+                for (int q = 0; q < RR; q++) {
+                    if (r + q < nr) {
+#pragma unroll
+                        for (int e = 0; e < PER; e++) Xs[(j0 + r + q) * LX + cq + e] = acc[q][e];
+                    }
+#pragma unroll
+                    for (int e = 0; e < PER; e++) acc[q][e] = T(0);
+                }
             } else {
                 // X_j -= sum of the gemm tasks, then the TS task: the nr x nr
                 // triangle by warp-shuffle substitution
@@ -274,10 +335,66 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
     }
 }
 
+// Diagonal-block inverses of one instance per CTA (FP32): warp w inverts the
+// forward-view blocks w, w + 8, ...: the lower triangle (unit diagonal when
+// flagged) goes to shared memory, lane c solves L x = e_c by forward
+// substitution in registers (x_r = 0 above the diagonal; rows past the
+// instance's order are the identity) and writes column c of the inverse,
+// k-major (Linv[c * 32 + r] = inverse(r, c)).
+struct InvJob {
+    const float *A;
+    float *Linv;
+    int64_t lda;
+    int k;
+    int flags;  // as Unit::flags (bit0 mt, bit1 rev, bit2 unit diagonal)
+};
+
+__global__ void __launch_bounds__(NT) batched_inv_kernel(const InvJob *__restrict__ jobs, int njobs)
+{
+    __shared__ float Ls[NT / 32][NBB][NBB + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int jj = blockIdx.x; jj < njobs; jj += gridDim.x) {
+        const InvJob J = jobs[jj];
+        Unit<float> u{};
+        u.A = J.A;
+        u.lda = J.lda;
+        u.k = J.k;
+        u.flags = J.flags;
+        const bool unitd = J.flags & 4;
+        const bool mt = J.flags & 1;
+        const int nblk = (J.k + NBB - 1) / NBB;
+        for (int b = warp; b < nblk; b += NT / 32) {
+            const int j0 = b * NBB, nr = min(NBB, J.k - j0);
+            // the block's lower triangle, read along A's contiguous dimension
+            for (int idx = lane; idx < NBB * NBB; idx += 32) {
+                const int fast = idx % NBB, slow = idx / NBB;
+                const int rr = mt ? slow : fast, cc = mt ? fast : slow;
+                float v = 0.f;
+                if (rr < nr && cc < nr && cc <= rr) v = *mv_addr(u, j0 + rr, j0 + cc);
+                if (rr == cc && (unitd || rr >= nr)) v = 1.f;
+                Ls[warp][rr][cc] = v;
+            }
+            __syncwarp();
+            float x[NBB];
+#pragma unroll
+            for (int r = 0; r < NBB; r++) {
+                float sum = (r == lane) ? 1.f : 0.f;
+#pragma unroll
+                for (int t = 0; t < r; t++) sum -= Ls[warp][r][t] * x[t];
+                x[r] = (r < lane) ? 0.f : sum / Ls[warp][r][r];
+            }
+            float *dst = J.Linv + size_t(b) * NBB * NBB + size_t(lane) * NBB;
+#pragma unroll
+            for (int r = 0; r < NBB; r++) dst[r] = x[r];
+            __syncwarp();
+        }
+    }
+}
+
 template <typename T, int RR>
 constexpr size_t batched_smem()
 {
-    return sizeof(T) * (size_t(KMAX) * BCfg<T, RR>::LX + NBUF * NBB * LT + NBB);
+    return sizeof(T) * (size_t(KMAX) * BCfg<T, RR>::LX + nbuf<T>() * NBB * LT + NBB);
 }
 
 }  // namespace
@@ -303,6 +420,11 @@ struct BatchedPlan {
     cudaGraphExec_t exec = nullptr;
     uint64_t graph_kernels = 0;
     double flops = 0, bytes = 0;
+    // FP32: inverses of every instance's diagonal blocks, recomputed each run
+    std::vector<InvJob> jobs_h;
+    InvJob *jobs = nullptr;
+    float *linv = nullptr;
+    size_t linv_elems = 0;
 };
 
 namespace {
@@ -328,11 +450,27 @@ void build_units(BatchedPlan &P, int64_t count, const int8_t *side, const int8_t
         const bool mt = left ? (trans[i] == GB_TRANS) : (trans[i] == GB_NOTRANS);
         const bool fwd = (uplo[i] == GB_LOWER) != mt;
         const int flags = (mt ? 1 : 0) | (fwd ? 0 : 2) | (diag[i] == GB_UNIT ? 4 : 0) | (left ? 8 : 0);
+        // FP32: the instance's block inverses at this element offset of the
+        // plan's inverse buffer (kept as offset + 1, 0 meaning none, until
+        // the pointer is filled in on upload)
+        size_t linv_off = 0;
+        if (sizeof(T) == 4) {
+            linv_off = P.linv_elems + 1;
+            P.linv_elems += size_t((k + NBB - 1) / NBB) * NBB * NBB;
+            InvJob j;
+            j.A = reinterpret_cast<const float *>(A[i]);
+            j.Linv = reinterpret_cast<float *>(linv_off);
+            j.lda = lda[i];
+            j.k = int(k);
+            j.flags = flags;
+            P.jobs_h.push_back(j);
+        }
         for (int64_t c0 = 0; c0 < ncols; c0 += CW) {
             Unit<T> u;
             u.A = static_cast<const T *>(A[i]);
             T *b = static_cast<T *>(B[i]);
             u.B = left ? b + c0 * ldb[i] : b + c0;
+            u.Linv = sizeof(T) == 4 ? reinterpret_cast<const T *>(linv_off) : nullptr;
             u.lda = lda[i];
             u.ldb = ldb[i];
             u.k = int(k);
@@ -354,6 +492,15 @@ int upload_and_capture(BatchedPlan &P, std::vector<Unit<T>> &units, cudaStream_t
     const size_t ub = units.size() * sizeof(Unit<T>);
     GB_CUDA(cudaMalloc(&P.units, ub > 0 ? ub : sizeof(Unit<T>)));
     GB_CUDA(cudaMalloc(&P.ticket, sizeof(unsigned)));
+    if (!P.jobs_h.empty()) {
+        GB_CUDA(cudaMalloc(&P.linv, P.linv_elems * sizeof(float)));
+        GB_CUDA(cudaMalloc(&P.jobs, P.jobs_h.size() * sizeof(InvJob)));
+        for (auto &j : P.jobs_h) j.Linv = P.linv + (reinterpret_cast<size_t>(j.Linv) - 1);
+        for (auto &u : units)
+            if (u.Linv) u.Linv = reinterpret_cast<const T *>(P.linv) + (reinterpret_cast<size_t>(u.Linv) - 1);
+        GB_CUDA(cudaMemcpyAsync(P.jobs, P.jobs_h.data(), P.jobs_h.size() * sizeof(InvJob), cudaMemcpyHostToDevice,
+                                s));
+    }
     if (ub) GB_CUDA(cudaMemcpyAsync(P.units, units.data(), ub, cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaStreamSynchronize(s));
     static PerDeviceOnce attr;
@@ -374,6 +521,12 @@ int upload_and_capture(BatchedPlan &P, std::vector<Unit<T>> &units, cudaStream_t
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(P.ticket, 0, sizeof(unsigned), cs);
+        if (!P.jobs_h.empty()) {
+            const int64_t nj = int64_t(P.jobs_h.size());
+            const int64_t gi = nj < int64_t(sms) * 8 ? nj : int64_t(sms) * 8;
+            LaunchScope ls(KK_BATCHED, cs, 0.0, 4.0 * double(P.linv_elems));
+            batched_inv_kernel<<<(unsigned)gi, NT, 0, cs>>>(P.jobs, int(nj));
+        }
         {
             LaunchScope ls(KK_BATCHED, cs, P.flops, P.bytes);
             batched_kernel<T, RR><<<P.grid, NT, batched_smem<T, RR>(), cs>>>(
@@ -418,6 +571,8 @@ void batched_free(BatchedPlan *P)
     if (P->exec) cudaGraphExecDestroy(P->exec);
     if (P->units) cudaFree(P->units);
     if (P->ticket) cudaFree(P->ticket);
+    if (P->jobs) cudaFree(P->jobs);
+    if (P->linv) cudaFree(P->linv);
     delete P;
 }
 
