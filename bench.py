@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--m", type=int, default=16384)
     p.add_argument("--n", type=int, default=16384)
-    p.add_argument("--path", default="mixed", choices=["mixed", "fp64", "batched"])
+    p.add_argument("--path", default="mixed", choices=["mixed", "fp64", "batched", "potrf"])
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="batched path precision")
     p.add_argument("--prec", default="bf16", choices=["bf16", "fp8"], help="mixed path low precision")
     p.add_argument("--count", type=int, default=4096, help="batched path: number of problems")
@@ -722,12 +722,44 @@ def run_batched(args):
     return 0
 
 
+def run_potrf(args):
+    """--path potrf: the Cholesky factorisation on this TRSM (gb_dpotrf,
+    FP64, lower) of an n x n symmetric diagonally dominant SPD matrix as the
+    timed step (A re-copied from a pristine device copy before each step,
+    outside the events); TFLOP/s of n^3/3."""
+    import torch
+
+    from paper_2305_19917_gb300 import api, inputs
+
+    torch.cuda.set_device(0)
+    api.lib()
+    n = args.n
+    stream = torch.cuda.current_stream()
+    S0 = inputs.make_spd_device(n, seed=5)
+    S = torch.empty_like(S0)
+    infos = []
+    t, _ = _time_calls(lambda: infos.append(api.potrf(0, S, stream=stream)), lambda: S.copy_(S0), args.steps,
+                       max(1, args.warmup), stream)
+    cols = [0, n // 2, n - 1]
+    L = torch.tril(S).cpu().numpy()
+    err = float(np.linalg.norm(L @ L[cols, :].T - S0[:, cols].cpu().numpy()) / np.linalg.norm(S0[:, cols].cpu().numpy()))
+    line = {"metric": "Cholesky TFLOP/s (n^3/3) on this TRSM", "value": float(n) ** 3 / 3 / (t * 1e-3) / 1e12,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"gb_dpotrf lower, n = {n}, symmetric diagonally dominant SPD (device seed 5)"},
+            "accuracy": {"info": infos[-1], "backward_err_sampled_cols": err}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.path == "batched":
         return run_batched(args)
+    if args.path == "potrf":
+        return run_potrf(args)
     return run_ours(args)
 
 
