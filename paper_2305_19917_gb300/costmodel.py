@@ -1,5 +1,5 @@
 """Learned cost model: training / inference driver for the library's CUDA MLP
-kernels, plus the plan-choice policies it is judged against.
+kernels, plus the plan-choice policies it is compared with.
 
 The network maps the 17 plan features of ``gb_plan_features`` to the log of
 the measured solve time.  It replaces the paper's analytical performance
@@ -7,7 +7,7 @@ models (Section V: ``Comp(i) = r(i) TS(i) + sum r(j) gemm(j)`` for the
 recursive model and its iterative / blocked counterparts, with the stop rule
 ``2 TS(i+1) < TS(i)``).  Those models, evaluated with task times measured on
 the GPU (PaperAnalyticPolicy), are "the method without the network" that it
-is judged against, beside a fitted-rates variant (AnalyticPolicy) and a
+is compared with, beside a fitted-rates variant (AnalyticPolicy) and a
 fixed plan.  The same network also predicts the mixed-precision solves, so
 the planner chooses the precision (plain FP64, BF16- or FP8-mixed, and the
 mixed solve's leaf order) for a request of FP64-level accuracy.
@@ -412,7 +412,7 @@ def precision_regret(test_rows, choose):
 def evaluate_precision(plan_rows, prec_rows, epochs=200, seed=0, prec_weight=8):
     """Train the network on the plan database plus the training shapes of the
     precision database (their rows repeated prec_weight times, they are few)
-    and judge its precision choice on the held-out precision shapes against
+    and evaluate its precision choice on the held-out precision shapes against
     exhaustive search, always-plain-FP64 and always-BF16 (leaf 1024)."""
     tr, te = split_prec_shapes(prec_rows, 0.8, seed)
     train = list(plan_rows) + prec_feature_rows(tr) * prec_weight

@@ -1,7 +1,7 @@
 """The learned cost model: trained on the GPU by the library's own kernels
 from the committed autotuner timings (420 shapes x 48 plans, m and n
 log-uniform in [64, 32768]; plus 150 FP64 shapes timed in plain FP64 and in
-five mixed-precision configurations), judged on held-out shapes (80/20
+five mixed-precision configurations), evaluated on held-out shapes (80/20
 split on shapes) by its regret t(chosen) / t(best) - 1 against exhaustive
 search; and what it gains over the method without it -- the paper's
 analytic models (Section V) with measured task times, a fitted-rates

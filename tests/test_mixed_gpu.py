@@ -88,6 +88,26 @@ def test_mixed_config_scale_sampled(m, n):
     assert fwd_err(X, Xo) <= 1e-10
 
 
+@pytest.mark.parametrize("side,uplo,trans,diag,prec", [(1, 1, 1, 0, 0), (0, 1, 1, 1, 0), (1, 0, 0, 0, 1)])
+def test_mixed_other_forms_config_scale_sampled(side, uplo, trans, diag, prec):
+    """Mixed solves in other forms at 16384^2 (a Right-side form transposes
+    B into the canonical view, an Upper form reverses the indices): sampled
+    rows (side Right: each row of X depends only on its row of B) or columns,
+    the last ones included, vs the oracle within 1e-10."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    m = n = 16384
+    A, B = inputs.make_problem_device(side, uplo, trans, diag, m, n, seed=70 + side + 2 * uplo)
+    idx = [0, 1, m // 2, m - 2, m - 1]
+    Bs = (B[idx, :] if side == 1 else B[:, idx]).cpu().numpy()
+    st, it, est = api.trsm_mixed(side, uplo, trans, diag, 1.5, A, B, tol=1e-11, prec=prec, max_iter=60)
+    torch.cuda.synchronize()
+    assert st == 0 and 1 <= it <= 12, (st, it, est, api.gb_mixed_history())
+    Xs = (B[idx, :] if side == 1 else B[:, idx]).cpu().numpy()
+    Xo = oracle.dtrsm(side, uplo, trans, diag, 1.5, A.cpu().numpy(), Bs)
+    assert fwd_err(Xs, Xo) <= 1e-10
+
+
 @pytest.mark.parametrize("m,n", [(16384, 16384), (32768, 4096)])
 def test_mixed_fp8_config_scale_sampled(m, n):
     """FP8 E4M3 updates (per-128x128-block power-of-two scales) at the
