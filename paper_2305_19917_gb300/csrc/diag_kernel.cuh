@@ -16,7 +16,25 @@
 namespace gb {
 namespace {
 
-constexpr int kDiagCols = 64;  // right-hand sides per CTA (one per thread)
+// Threads per CTA; a CTA solves CW = 64 right-hand sides, one per thread.
+// (Narrower CTAs for narrow problems were measured and do not help: a warp
+// runs on one SM sub-partition, whose FP64 unit takes about 64 clocks per
+// warp instruction whatever the number of active lanes, so a column's
+// substitution costs the same in any CTA shape.)
+constexpr int kDiagThreads = 64;
+
+// Asynchronous copy of one 4- or 8-byte element into shared memory; `in`
+// false writes zero (the source is not read).
+template <typename T>
+__device__ __forceinline__ void diag_cp_async(T *dst, const T *src, bool in)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    const int n = in ? int(sizeof(T)) : 0;
+    if (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
 
 template <typename T>
 struct Vec;
@@ -35,19 +53,19 @@ struct Vec<double> {
 //   L  [NB][NB]   column form (MT=false): L[k*NB + i] = Mv(i,k)
 //                 row form    (MT=true) : L[i*NB + k] = Mv(i,k)
 //   inv[NB]       1 / Mv(i,i)  (1 for a unit diagonal or padding rows)
-//   Bs [NB][kDiagCols + 1]
-template <typename T, int NB>
+//   Bs [NB][CW + 1]
+template <typename T, int NB, int CW>
 constexpr size_t diag_smem_bytes()
 {
-    return sizeof(T) * (size_t(NB) * NB + NB + size_t(NB) * (kDiagCols + 1));
+    return sizeof(T) * (size_t(NB) * NB + NB + size_t(NB) * (CW + 1));
 }
 
 // FWD: Mv lower (forward substitution); MT: Mv(i,j) = A(j,i); LEFT: Bv
 // column-major.  Msub = &A(r0, r0), Bsub = &Bv(r0, 0).
 // EMIT: also write a BF16 copy of the solved block to Ebf (column-major,
 // ldb), the operand of the tensor-core GEMM updates (LEFT layout only).
-template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT>
-__global__ void __launch_bounds__(kDiagCols)
+template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT, int CW>
+__global__ void __launch_bounds__(kDiagThreads)
 diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
                   int64_t ldb, int nr, int64_t ncols, T alpha, int unit,
                   __nv_bfloat16 *__restrict__ Ebf)
@@ -56,131 +74,135 @@ diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
     T *L = reinterpret_cast<T *>(smem_raw);
     T *inv = L + NB * NB;
     T *Bs = inv + NB;
-    constexpr int BS = kDiagCols + 1;
+    constexpr int BS = CW + 1;
 
     const int tid = threadIdx.x;
-    const int64_t c0 = int64_t(blockIdx.x) * kDiagCols;
-    const int ncb = (int)((ncols - c0) < kDiagCols ? (ncols - c0) : kDiagCols);
+    const int64_t c0 = int64_t(blockIdx.x) * CW;
+    const int ncb = (int)((ncols - c0) < CW ? (ncols - c0) : CW);
 
-    // ---- triangle -> shared memory (only the referenced strict triangle) --
-    // Global A is column-major; Mv(i,k) = MT ? A(k,i) : A(i,k).  The loop
-    // index runs fastest over A's contiguous dimension.
-    for (int idx = tid; idx < NB * NB; idx += kDiagCols) {
+    // ---- triangle and B panel -> shared memory, as asynchronous copies ----
+    // (every copy of the thread in flight at once: a loop of load-then-store
+    // would wait out the memory latency once per element).  Global A is
+    // column-major; Mv(i,k) = MT ? A(k,i) : A(i,k).  The loop index runs
+    // fastest over A's contiguous dimension; entries outside the referenced
+    // strict triangle are zero-filled.
+    for (int idx = tid; idx < NB * NB; idx += kDiagThreads) {
         int fast = idx % NB, slow = idx / NB;  // fast = row of A, slow = col of A
         int i = MT ? slow : fast;              // row of Mv
         int k = MT ? fast : slow;              // col of Mv
         bool ref = (i < nr) && (k < nr) && (FWD ? (k < i) : (k > i));
-        T v = ref ? Msub[fast + int64_t(slow) * lda] : T(0);
         // column form stores Mv(:,k) contiguously, row form Mv(i,:)
-        L[MT ? (i * NB + k) : (k * NB + i)] = v;
+        diag_cp_async(&L[MT ? (i * NB + k) : (k * NB + i)], ref ? Msub + fast + int64_t(slow) * lda : Msub, ref);
     }
-    for (int i = tid; i < NB; i += kDiagCols) {
+    // B panel, coalesced
+    if (LEFT) {  // Bv(i,c) = Bsub[i + c*ldb]: contiguous in i
+        for (int idx = tid; idx < NB * CW; idx += kDiagThreads) {
+            int i = idx % NB, c = idx / NB;
+            const bool in = i < nr && c < ncb;
+            diag_cp_async(&Bs[i * BS + c], in ? Bsub + i + (c0 + c) * ldb : Bsub, in);
+        }
+    } else {     // Bv(i,c) = Bsub[c + i*ldb]: contiguous in c
+        for (int idx = tid; idx < NB * CW; idx += kDiagThreads) {
+            int c = idx % CW, i = idx / CW;
+            const bool in = i < nr && c < ncb;
+            diag_cp_async(&Bs[i * BS + c], in ? Bsub + (c0 + c) + int64_t(i) * ldb : Bsub, in);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int i = tid; i < NB; i += kDiagThreads) {
         T d = T(1);
         if (i < nr && !unit) d = T(1) / Msub[i + int64_t(i) * lda];
         inv[i] = d;
     }
-    // ---- B panel -> shared memory, coalesced ------------------------------
-    if (LEFT) {  // Bv(i,c) = Bsub[i + c*ldb]: contiguous in i
-        for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
-            int i = idx % NB, c = idx / NB;
-            T v = T(0);
-            if (i < nr && c < ncb) v = Bsub[i + (c0 + c) * ldb];
-            Bs[i * BS + c] = v;
-        }
-    } else {     // Bv(i,c) = Bsub[c + i*ldb]: contiguous in c
-        for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
-            int c = idx % kDiagCols, i = idx / kDiagCols;
-            T v = T(0);
-            if (i < nr && c < ncb) v = Bsub[(c0 + c) + int64_t(i) * ldb];
-            Bs[i * BS + c] = v;
-        }
-    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 
-    // ---- substitution in registers ----------------------------------------
-    T t[NB];
+    // ---- substitution in registers (one thread per right-hand side) ---------
+    if (tid < CW) {
+        T t[NB];
 #pragma unroll
-    for (int i = 0; i < NB; i++) t[i] = alpha * Bs[i * BS + tid];
+        for (int i = 0; i < NB; i++) t[i] = alpha * Bs[i * BS + tid];
 
-    using V = typename Vec<T>::type;
-    constexpr int VN = Vec<T>::n;
-    if (!MT) {
-        // column (axpy) form: once x_k is known, subtract Mv(:,k) x_k
-        if (FWD) {
+        using V = typename Vec<T>::type;
+        constexpr int VN = Vec<T>::n;
+        if (!MT) {
+            // column (axpy) form: once x_k is known, subtract Mv(:,k) x_k
+            if (FWD) {
 #pragma unroll
-            for (int k = 0; k < NB; k++) {
-                T x = t[k] * inv[k];
-                t[k] = x;
+                for (int k = 0; k < NB; k++) {
+                    T x = t[k] * inv[k];
+                    t[k] = x;
 #pragma unroll
-                for (int i0 = ((k + 1) / VN) * VN; i0 < NB; i0 += VN) {
-                    V v = *reinterpret_cast<const V *>(&L[k * NB + i0]);
-                    const T *vv = reinterpret_cast<const T *>(&v);
+                    for (int i0 = ((k + 1) / VN) * VN; i0 < NB; i0 += VN) {
+                        V v = *reinterpret_cast<const V *>(&L[k * NB + i0]);
+                        const T *vv = reinterpret_cast<const T *>(&v);
 #pragma unroll
-                    for (int e = 0; e < VN; e++)
-                        if (i0 + e > k) t[i0 + e] -= vv[e] * x;
+                        for (int e = 0; e < VN; e++)
+                            if (i0 + e > k) t[i0 + e] -= vv[e] * x;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = NB - 1; k >= 0; k--) {
+                    T x = t[k] * inv[k];
+                    t[k] = x;
+#pragma unroll
+                    for (int i0 = 0; i0 < k; i0 += VN) {
+                        V v = *reinterpret_cast<const V *>(&L[k * NB + i0]);
+                        const T *vv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                        for (int e = 0; e < VN; e++)
+                            if (i0 + e < k) t[i0 + e] -= vv[e] * x;
+                    }
                 }
             }
         } else {
+            // row (dot) form: x_i = (t_i - Mv(i,:) x) / Mv(i,i), two partial sums
+            if (FWD) {
 #pragma unroll
-            for (int k = NB - 1; k >= 0; k--) {
-                T x = t[k] * inv[k];
-                t[k] = x;
+                for (int i = 0; i < NB; i++) {
+                    T s0 = t[i], s1 = T(0);
 #pragma unroll
-                for (int i0 = 0; i0 < k; i0 += VN) {
-                    V v = *reinterpret_cast<const V *>(&L[k * NB + i0]);
-                    const T *vv = reinterpret_cast<const T *>(&v);
+                    for (int k0 = 0; k0 < i; k0 += VN) {
+                        V v = *reinterpret_cast<const V *>(&L[i * NB + k0]);
+                        const T *vv = reinterpret_cast<const T *>(&v);
 #pragma unroll
-                    for (int e = 0; e < VN; e++)
-                        if (i0 + e < k) t[i0 + e] -= vv[e] * x;
+                        for (int e = 0; e < VN; e++)
+                            if (k0 + e < i) {
+                                if (((k0 + e) & 1) == 0) s0 -= vv[e] * t[k0 + e];
+                                else s1 -= vv[e] * t[k0 + e];
+                            }
+                    }
+                    t[i] = (s0 + s1) * inv[i];
+                }
+            } else {
+#pragma unroll
+                for (int i = NB - 1; i >= 0; i--) {
+                    T s0 = t[i], s1 = T(0);
+#pragma unroll
+                    for (int k0 = ((i + 1) / VN) * VN; k0 < NB; k0 += VN) {
+                        V v = *reinterpret_cast<const V *>(&L[i * NB + k0]);
+                        const T *vv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                        for (int e = 0; e < VN; e++)
+                            if (k0 + e > i) {
+                                if (((k0 + e) & 1) == 0) s0 -= vv[e] * t[k0 + e];
+                                else s1 -= vv[e] * t[k0 + e];
+                            }
+                    }
+                    t[i] = (s0 + s1) * inv[i];
                 }
             }
         }
-    } else {
-        // row (dot) form: x_i = (t_i - Mv(i,:) x) / Mv(i,i), two partial sums
-        if (FWD) {
+
 #pragma unroll
-            for (int i = 0; i < NB; i++) {
-                T s0 = t[i], s1 = T(0);
-#pragma unroll
-                for (int k0 = 0; k0 < i; k0 += VN) {
-                    V v = *reinterpret_cast<const V *>(&L[i * NB + k0]);
-                    const T *vv = reinterpret_cast<const T *>(&v);
-#pragma unroll
-                    for (int e = 0; e < VN; e++)
-                        if (k0 + e < i) {
-                            if (((k0 + e) & 1) == 0) s0 -= vv[e] * t[k0 + e];
-                            else s1 -= vv[e] * t[k0 + e];
-                        }
-                }
-                t[i] = (s0 + s1) * inv[i];
-            }
-        } else {
-#pragma unroll
-            for (int i = NB - 1; i >= 0; i--) {
-                T s0 = t[i], s1 = T(0);
-#pragma unroll
-                for (int k0 = ((i + 1) / VN) * VN; k0 < NB; k0 += VN) {
-                    V v = *reinterpret_cast<const V *>(&L[i * NB + k0]);
-                    const T *vv = reinterpret_cast<const T *>(&v);
-#pragma unroll
-                    for (int e = 0; e < VN; e++)
-                        if (k0 + e > i) {
-                            if (((k0 + e) & 1) == 0) s0 -= vv[e] * t[k0 + e];
-                            else s1 -= vv[e] * t[k0 + e];
-                        }
-                }
-                t[i] = (s0 + s1) * inv[i];
-            }
-        }
+        for (int i = 0; i < NB; i++) Bs[i * BS + tid] = t[i];
     }
-
-#pragma unroll
-    for (int i = 0; i < NB; i++) Bs[i * BS + tid] = t[i];
     __syncthreads();
 
     // ---- write back, coalesced --------------------------------------------
     if (LEFT) {
-        for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
+        for (int idx = tid; idx < NB * CW; idx += kDiagThreads) {
             int i = idx % NB, c = idx / NB;
             if (i < nr && c < ncb) {
                 Bsub[i + (c0 + c) * ldb] = Bs[i * BS + c];
@@ -188,37 +210,45 @@ diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
             }
         }
     } else {
-        for (int idx = tid; idx < NB * kDiagCols; idx += kDiagCols) {
-            int c = idx % kDiagCols, i = idx / kDiagCols;
+        for (int idx = tid; idx < NB * CW; idx += kDiagThreads) {
+            int c = idx % CW, i = idx / CW;
             if (i < nr && c < ncb) Bsub[(c0 + c) + int64_t(i) * ldb] = Bs[i * BS + c];
         }
     }
 }
 
 // One-time kernel attribute (dynamic shared memory above 48 KB).
-template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT>
+template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT, int CW>
 int diag_prepare()
 {
     static PerDeviceOnce attr;  // per instantiation and device
-    return smem_attr_once(attr, diag_solve_kernel<T, NB, FWD, MT, LEFT, EMIT>, diag_smem_bytes<T, NB>());
+    return smem_attr_once(attr, diag_solve_kernel<T, NB, FWD, MT, LEFT, EMIT, CW>, diag_smem_bytes<T, NB, CW>());
+}
+
+template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT, int CW>
+int launch_nb_cw(const T *Msub, int64_t lda, T *Bsub, int64_t ldb, int nr, int64_t ncols, T alpha, int unit,
+                 cudaStream_t s, __nv_bfloat16 *Ebf)
+{
+    auto kern = diag_solve_kernel<T, NB, FWD, MT, LEFT, EMIT, CW>;
+    constexpr size_t smem = diag_smem_bytes<T, NB, CW>();
+    {
+        const int pst = diag_prepare<T, NB, FWD, MT, LEFT, EMIT, CW>();
+        if (pst) return pst;
+    }
+    int64_t grid = (ncols + CW - 1) / CW;
+    if (grid > 0x7fffffff) return GB_STATUS_CUDA_ERROR;
+    LaunchScope ls(KK_DIAG, s, double(nr) * nr * ncols,
+                   sizeof(T) * (0.5 * nr * nr + 2.0 * nr * ncols));
+    kern<<<(unsigned)grid, kDiagThreads, smem, s>>>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit, Ebf);
+    return check(cudaGetLastError());
 }
 
 template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT = false>
 int launch_nb(const T *Msub, int64_t lda, T *Bsub, int64_t ldb, int nr, int64_t ncols,
               T alpha, int unit, cudaStream_t s, __nv_bfloat16 *Ebf = nullptr)
 {
-    auto kern = diag_solve_kernel<T, NB, FWD, MT, LEFT, EMIT>;
-    constexpr size_t smem = diag_smem_bytes<T, NB>();
-    {
-        const int pst = diag_prepare<T, NB, FWD, MT, LEFT, EMIT>();
-        if (pst) return pst;
-    }
-    int64_t grid = (ncols + kDiagCols - 1) / kDiagCols;
-    if (grid > 0x7fffffff) return GB_STATUS_CUDA_ERROR;
-    LaunchScope ls(KK_DIAG, s, double(nr) * nr * ncols,
-                   sizeof(T) * (0.5 * nr * nr + 2.0 * nr * ncols));
-    kern<<<(unsigned)grid, kDiagCols, smem, s>>>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit, Ebf);
-    return check(cudaGetLastError());
+    return launch_nb_cw<T, NB, FWD, MT, LEFT, EMIT, kDiagThreads>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit, s,
+                                                                  Ebf);
 }
 
 template <typename T, bool FWD, bool MT, bool LEFT>
