@@ -2,13 +2,20 @@
 // and 3; the white triangles of Figs. 2-4), for one nr x nr block with
 // nr <= 64 and all right-hand sides of the canonical view.
 //
-// Design (GB300): one thread owns one right-hand side; its nb entries live in
-// registers for the whole solve (fully unrolled substitution), the triangle
-// sits in shared memory and is read with broadcast vector loads, and the B
-// panel is staged through shared memory so that global loads and stores are
-// coalesced whichever way B is laid out.  The diagonal is inverted once per
-// CTA, so each step is a multiply (FP64: DFMA-bound; the whole block costs
-// nr^2/2 multiply-adds per right-hand side).
+// Design (GB300): a CTA solves 64 right-hand sides with 8 warps; warp w
+// handles 32 of them (column group w / 4) and the rows i = w % 4 (mod 4) of
+// the block, in registers, by column-oriented substitution: at step k the
+// warp owning row k forms x_k = t_k / a_kk, publishes it in shared memory
+// (a named barrier per column group), and the four warps update their own
+// rows.  Splitting each right-hand side's rows over four warps matters on
+// this GPU: a warp runs on one SM sub-partition, whose FP64 unit takes about
+// 64 clocks per warp instruction (a quarter of the SM's 1.9 DFMA per clock),
+// so one warp per column would leave three quarters of the FP64 throughput
+// idle and make the serial chain four times longer.  The triangle sits in
+// shared memory (broadcast reads), the B panel is staged through shared
+// memory with asynchronous copies so that global loads and stores are
+// coalesced whichever way B is laid out, and the diagonal is inverted once
+// per CTA (nr^2/2 multiply-adds per right-hand side).
 #pragma once
 #include <cuda_bf16.h>
 #include "common.cuh"
@@ -16,12 +23,9 @@
 namespace gb {
 namespace {
 
-// Threads per CTA; a CTA solves CW = 64 right-hand sides, one per thread.
-// (Narrower CTAs for narrow problems were measured and do not help: a warp
-// runs on one SM sub-partition, whose FP64 unit takes about 64 clocks per
-// warp instruction whatever the number of active lanes, so a column's
-// substitution costs the same in any CTA shape.)
-constexpr int kDiagThreads = 64;
+// Threads per CTA (8 warps: 2 column groups x 4 row groups); a CTA solves
+// CW = 64 right-hand sides.
+constexpr int kDiagThreads = 256;
 
 // Asynchronous copy of one 4- or 8-byte element into shared memory; `in`
 // false writes zero (the source is not read).
@@ -36,19 +40,6 @@ __device__ __forceinline__ void diag_cp_async(T *dst, const T *src, bool in)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
-template <typename T>
-struct Vec;
-template <>
-struct Vec<float> {
-    using type = float4;
-    static constexpr int n = 4;
-};
-template <>
-struct Vec<double> {
-    using type = double2;
-    static constexpr int n = 2;
-};
-
 // Shared-memory layout (dynamic):
 //   L  [NB][NB]   column form (MT=false): L[k*NB + i] = Mv(i,k)
 //                 row form    (MT=true) : L[i*NB + k] = Mv(i,k)
@@ -58,6 +49,45 @@ template <typename T, int NB, int CW>
 constexpr size_t diag_smem_bytes()
 {
     return sizeof(T) * (size_t(NB) * NB + NB + size_t(NB) * (CW + 1));
+}
+
+// The substitution of one warp: rows i = 4 m + RG of right-hand side `col`
+// (column group cg).  At step k the warp owning row k forms x_k = t_k / a_kk
+// and publishes it in Bs (row k); after the column group's named barrier the
+// four warps subtract a_ik x_k from their rows below (forward) or above
+// (backward) k.  Fully unrolled with RG fixed, so t stays in registers and
+// every row test is a compile-time constant.  The four warps of a column
+// group run different instantiations and meet at the same named barrier
+// (a counting barrier of 128 threads) from their own code.
+template <typename T, int NB, bool FWD, bool MT, int CW, int RG>
+__device__ __forceinline__ void diag_rows(const T *L, const T *inv, T *Bs, int nr, int col, int cg, T alpha)
+{
+    constexpr int BS = CW + 1;
+    constexpr int NM = NB / 4;
+    T t[NM];
+    // a warp reads only its own rows of B, and x_k overwrites row k, owned by
+    // the warp that writes it: no barrier needed before the steps
+#pragma unroll
+    for (int m = 0; m < NM; m++) t[m] = alpha * Bs[(4 * m + RG) * BS + col];
+    const uint32_t bar_id = 1u + uint32_t(cg);
+#pragma unroll
+    for (int s = 0; s < NB; s++) {
+        const int k = FWD ? s : NB - 1 - s;
+        if (k < nr) {
+            if ((k & 3) == RG) {
+                const T x = t[k >> 2] * inv[k];
+                t[k >> 2] = x;
+                Bs[k * BS + col] = x;
+            }
+            asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+            const T x = Bs[k * BS + col];
+#pragma unroll
+            for (int m = 0; m < NM; m++) {
+                const int i = 4 * m + RG;
+                if (FWD ? (i > k) : (i < k)) t[m] -= (MT ? L[i * NB + k] : L[k * NB + i]) * x;
+            }
+        }
+    }
 }
 
 // FWD: Mv lower (forward substitution); MT: Mv(i,j) = A(j,i); LEFT: Bv
@@ -117,86 +147,22 @@ diag_solve_kernel(const T *__restrict__ Msub, int64_t lda, T *__restrict__ Bsub,
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 
-    // ---- substitution in registers (one thread per right-hand side) ---------
-    if (tid < CW) {
-        T t[NB];
-#pragma unroll
-        for (int i = 0; i < NB; i++) t[i] = alpha * Bs[i * BS + tid];
-
-        using V = typename Vec<T>::type;
-        constexpr int VN = Vec<T>::n;
-        if (!MT) {
-            // column (axpy) form: once x_k is known, subtract Mv(:,k) x_k
-            if (FWD) {
-#pragma unroll
-                for (int k = 0; k < NB; k++) {
-                    T x = t[k] * inv[k];
-                    t[k] = x;
-#pragma unroll
-                    for (int i0 = ((k + 1) / VN) * VN; i0 < NB; i0 += VN) {
-                        V v = *reinterpret_cast<const V *>(&L[k * NB + i0]);
-                        const T *vv = reinterpret_cast<const T *>(&v);
-#pragma unroll
-                        for (int e = 0; e < VN; e++)
-                            if (i0 + e > k) t[i0 + e] -= vv[e] * x;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int k = NB - 1; k >= 0; k--) {
-                    T x = t[k] * inv[k];
-                    t[k] = x;
-#pragma unroll
-                    for (int i0 = 0; i0 < k; i0 += VN) {
-                        V v = *reinterpret_cast<const V *>(&L[k * NB + i0]);
-                        const T *vv = reinterpret_cast<const T *>(&v);
-#pragma unroll
-                        for (int e = 0; e < VN; e++)
-                            if (i0 + e < k) t[i0 + e] -= vv[e] * x;
-                    }
-                }
-            }
-        } else {
-            // row (dot) form: x_i = (t_i - Mv(i,:) x) / Mv(i,i), two partial sums
-            if (FWD) {
-#pragma unroll
-                for (int i = 0; i < NB; i++) {
-                    T s0 = t[i], s1 = T(0);
-#pragma unroll
-                    for (int k0 = 0; k0 < i; k0 += VN) {
-                        V v = *reinterpret_cast<const V *>(&L[i * NB + k0]);
-                        const T *vv = reinterpret_cast<const T *>(&v);
-#pragma unroll
-                        for (int e = 0; e < VN; e++)
-                            if (k0 + e < i) {
-                                if (((k0 + e) & 1) == 0) s0 -= vv[e] * t[k0 + e];
-                                else s1 -= vv[e] * t[k0 + e];
-                            }
-                    }
-                    t[i] = (s0 + s1) * inv[i];
-                }
-            } else {
-#pragma unroll
-                for (int i = NB - 1; i >= 0; i--) {
-                    T s0 = t[i], s1 = T(0);
-#pragma unroll
-                    for (int k0 = ((i + 1) / VN) * VN; k0 < NB; k0 += VN) {
-                        V v = *reinterpret_cast<const V *>(&L[i * NB + k0]);
-                        const T *vv = reinterpret_cast<const T *>(&v);
-#pragma unroll
-                        for (int e = 0; e < VN; e++)
-                            if (k0 + e > i) {
-                                if (((k0 + e) & 1) == 0) s0 -= vv[e] * t[k0 + e];
-                                else s1 -= vv[e] * t[k0 + e];
-                            }
-                    }
-                    t[i] = (s0 + s1) * inv[i];
-                }
-            }
+    // ---- substitution: rows split over the four warps of a column group -----
+    // Bs holds B on entry; once every thread has its rows in registers it
+    // holds the published x_k (row k of the solved block).
+    {
+        const int warp = tid >> 5, lane = tid & 31;
+        const int cg = warp >> 2, rg = warp & 3;
+        const int col = cg * 32 + lane;
+        // one code path per row group, so that every row test is resolved at
+        // compile time (no predicated-off FP64 instructions)
+        switch (rg) {
+        case 0: diag_rows<T, NB, FWD, MT, CW, 0>(L, inv, Bs, nr, col, cg, alpha); break;
+        case 1: diag_rows<T, NB, FWD, MT, CW, 1>(L, inv, Bs, nr, col, cg, alpha); break;
+        case 2: diag_rows<T, NB, FWD, MT, CW, 2>(L, inv, Bs, nr, col, cg, alpha); break;
+        default: diag_rows<T, NB, FWD, MT, CW, 3>(L, inv, Bs, nr, col, cg, alpha); break;
         }
-
-#pragma unroll
-        for (int i = 0; i < NB; i++) Bs[i * BS + tid] = t[i];
+        // Bs now holds x_k in row k for every k < nr: the solved block
     }
     __syncthreads();
 
@@ -247,8 +213,7 @@ template <typename T, int NB, bool FWD, bool MT, bool LEFT, bool EMIT = false>
 int launch_nb(const T *Msub, int64_t lda, T *Bsub, int64_t ldb, int nr, int64_t ncols,
               T alpha, int unit, cudaStream_t s, __nv_bfloat16 *Ebf = nullptr)
 {
-    return launch_nb_cw<T, NB, FWD, MT, LEFT, EMIT, kDiagThreads>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit, s,
-                                                                  Ebf);
+    return launch_nb_cw<T, NB, FWD, MT, LEFT, EMIT, 64>(Msub, lda, Bsub, ldb, nr, ncols, alpha, unit, s, Ebf);
 }
 
 template <typename T, bool FWD, bool MT, bool LEFT>
