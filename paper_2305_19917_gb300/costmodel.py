@@ -409,7 +409,7 @@ def precision_regret(test_rows, choose):
     return np.array(out)
 
 
-def evaluate_precision(plan_rows, prec_rows, epochs=200, seed=0, prec_weight=8):
+def evaluate_precision(plan_rows, prec_rows, epochs=400, seed=0, prec_weight=8):
     """Train the network on the plan database plus the training shapes of the
     precision database (their rows repeated prec_weight times, they are few)
     and evaluate its precision choice on the held-out precision shapes against
@@ -431,7 +431,7 @@ def evaluate_precision(plan_rows, prec_rows, epochs=200, seed=0, prec_weight=8):
                        mixed_infeasible=int(sum(1 for r in prec_rows if not feasible(r))))
 
 
-def train_default_model(out=None, epochs=400, prec_weight=8):
+def train_default_model(out=None, epochs=800, prec_weight=8):
     """The committed planner network: trained on every row of the plan and
     precision databases (on the GPU, by the library's kernels) and saved."""
     rows = load_db(DEFAULT_DB)
@@ -454,7 +454,7 @@ def main(argv=None):
     p = argparse.ArgumentParser(description="train / evaluate the planner network")
     p.add_argument("--train", action="store_true", help="train on every row and save the model")
     p.add_argument("--out", default=None)
-    p.add_argument("--epochs", type=int, default=400)
+    p.add_argument("--epochs", type=int, default=800)
     p.add_argument("--evaluate", action="store_true", help="held-out regret of every policy")
     a = p.parse_args(argv)
     import torch
@@ -463,7 +463,7 @@ def main(argv=None):
     if a.evaluate:
         rows = load_db(DEFAULT_DB)
         tr, te = split_shapes(rows, 0.8, seed=0)
-        _, st = evaluate(tr, te, epochs=200, components=load_components(DEFAULT_COMP_DB))
+        _, st = evaluate(tr, te, epochs=800, components=load_components(DEFAULT_COMP_DB))
         print(json.dumps({"plans": st}))
         if os.path.exists(DEFAULT_PREC_DB):
             _, sp = evaluate_precision(rows, load_db(DEFAULT_PREC_DB))
