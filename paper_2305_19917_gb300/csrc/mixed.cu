@@ -268,35 +268,6 @@ __global__ void block_scales_kernel(const unsigned *bmax, float *bscale, int64_t
     }
 }
 
-// Round-to-nearest-even BF16 of a double, from its bit pattern (integer
-// operations only; results below the BF16 normal range flush to zero).
-__device__ __forceinline__ __nv_bfloat16 d2bf16(double a)
-{
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a));
-    const unsigned s = unsigned(b >> 63) << 15;
-    const int E = int((b >> 52) & 0x7FF);
-    const unsigned long long m = b & ((1ull << 52) - 1);
-    unsigned short out;
-    if (E == 0x7FF) {
-        out = (unsigned short)(s | 0x7F80u | (m ? 0x40u : 0u));
-    } else {
-        int e = E - 1023 + 127;
-        if (E == 0 || e <= 0) {
-            out = (unsigned short)s;
-        } else {
-            unsigned m7 = unsigned(m >> 45);
-            const unsigned long long rem = m & ((1ull << 45) - 1), half = 1ull << 44;
-            if (rem > half || (rem == half && (m7 & 1u))) m7++;
-            if (m7 == 128u) {
-                m7 = 0;
-                e++;
-            }
-            out = (e >= 255) ? (unsigned short)(s | 0x7F80u) : (unsigned short)(s | (unsigned(e) << 7) | m7);
-        }
-    }
-    return __ushort_as_bfloat16(out);
-}
-
 // The 48-bit fixed-point value N = round(a 2^(48-e)) of |a| < 2^(e-1)
 // (|N| <= 2^47), computed from the bit pattern with integer operations.
 __device__ __forceinline__ long long fixed48(double a, int e)
@@ -314,8 +285,44 @@ __device__ __forceinline__ long long fixed48(double a, int e)
     return (b >> 63) ? -n : n;
 }
 
+// Balanced base-256 digit of x: the d in [-128, 127] with d = x (mod 256).
+__device__ __forceinline__ int bal8(int x) { return ((x + 128) & 255) - 128; }
+// The FP32 bit pattern of an integer |d| < 2^22, exactly: d added to the
+// integer bits of 1.5 2^23 adds d to that value, which is then subtracted.
+__device__ __forceinline__ uint32_t small_int_f32bits(int d)
+{
+    return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f);
+}
+// Two BF16 in one word from FP32 patterns whose low 16 bits are zero (the
+// high halves are then the BF16 values exactly): lo_elem first.
+__device__ __forceinline__ uint32_t pack_hi16(uint32_t lo_elem, uint32_t hi_elem)
+{
+    return __byte_perm(lo_elem, hi_elem, 0x7632);
+}
+// Round-to-nearest-even BF16 bit pattern of a double, from the two 32-bit
+// halves of its bit pattern (as d2bf16: results below the BF16 normal range
+// flush to zero, overflow gives infinity, NaN stays NaN).
+__device__ __forceinline__ uint32_t d2bf16_bits(double a)
+{
+    const uint32_t hi = uint32_t(__double2hiint(a)), lo = uint32_t(__double2loint(a));
+    const uint32_t s = (hi >> 16) & 0x8000u;
+    const int E = int((hi >> 20) & 0x7FFu);
+    if (E == 0x7FF) return s | 0x7F80u | (((hi & 0xFFFFFu) | lo) ? 0x40u : 0u);
+    const int e = E - 1023 + 127;
+    if (E == 0 || e <= 0) return s;
+    uint32_t m7 = (hi >> 13) & 0x7Fu;        // mantissa bits 51..45
+    const uint32_t rem = hi & 0x1FFFu;       // bits 44..32 (bits 31..0 in lo)
+    if (rem > 0x1000u || (rem == 0x1000u && (lo != 0u || (m7 & 1u)))) m7++;
+    uint32_t r = (uint32_t(e) << 7) + m7;    // a carry out of m7 raises the exponent
+    if (r >= 0x7F80u) r = 0x7F80u;
+    return s | r;
+}
+
 // Pass 2: BF16 copy (round to nearest), the 6 digit slices of the strictly
 // lower part, the FP64 diagonal and the FP32 band of diagonal 64-blocks.
+// Thread tid takes 8 consecutive columns (8 (tid & 7) ..) of rows
+// (tid >> 3) and (tid >> 3) + 32 of the tile, so that every row-major output
+// is written 16 bytes at a time.
 __global__ void __launch_bounds__(256)
 prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bfloat16 *As, float *band,
              double *dg, uint8_t *A8, const float *bscale)
@@ -327,27 +334,62 @@ prepA_kernel(View v, int64_t kp, const int *e_row, __nv_bfloat16 *Abf, __nv_bflo
     __syncthreads();
     const int tid = threadIdx.x;
     const size_t slice = size_t(kp) * size_t(kp);
-    for (int idx = tid; idx < 64 * 64; idx += 256) {
-        int lc = idx & 63, li = idx >> 6;  // contiguous along c in the row-major outputs
-        int64_t i = i0 + li, c = c0 + lc;
-        double a = t[li][lc];
-        size_t off = size_t(i) * size_t(kp) + size_t(c);
-        Abf[off] = d2bf16(a);
-        if (A8 && (c >> 7) < (i >> 7))
-            A8[off] = __nv_cvt_float_to_fp8(f64_to_f32_rn(a) / bscale[(i >> 7) * (kp >> 7) + (c >> 7)], __NV_SATFINITE,
-                                            __NV_E4M3);
-        // balanced base-256 digits of N = round(a 2^(48-e)): N = sum_p q_p 256^(6-p),
-        // q_p in [-128, 128]; least significant first
-        long long N = (c == i) ? 0 : fixed48(a, e_row[i]);
-        if (c == i) dg[i] = a;
+    const int lc0 = (tid & 7) * 8;
+    const int64_t c8 = c0 + lc0;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; pass++) {
+        const int li = (tid >> 3) + 32 * pass;
+        const int64_t i = i0 + li;
+        const int e = e_row[i];
+        const size_t off = size_t(i) * size_t(kp) + size_t(c8);
+        uint32_t wbf[4], wd[kSlices][4];
+        uint32_t w8[2] = {0u, 0u};
+        const bool fp8 = A8 && (c8 >> 7) < (i >> 7);
+        const float sc = fp8 ? bscale[(i >> 7) * (kp >> 7) + (c8 >> 7)] : 1.f;
 #pragma unroll
-        for (int p = kSlices - 1; p >= 1; p--) {
-            const long long d = ((N + 128) & 255) - 128;
-            As[p * slice + off] = __int2bfloat16_rn(int(d));  // exact: |d| <= 128 has <= 8 significant bits
-            N = (N - d) >> 8;
+        for (int u = 0; u < 8; u += 2) {
+            uint32_t hb[2], dig[2][kSlices];
+#pragma unroll
+            for (int v2 = 0; v2 < 2; v2++) {
+                const int64_t c = c8 + u + v2;
+                const double a = t[li][lc0 + u + v2];
+                hb[v2] = d2bf16_bits(a);
+                if (fp8) {
+                    const unsigned q = __nv_cvt_float_to_fp8(f64_to_f32_rn(a) / sc, __NV_SATFINITE, __NV_E4M3);
+                    w8[(u + v2) >> 2] |= q << (8 * ((u + v2) & 3));
+                }
+                // balanced base-256 digits of N = round(a 2^(48-e)): N = sum_p q_p 256^(5-p),
+                // q_p in [-128, 127] for p >= 1 (least significant first), the top one
+                // q_0 in [-128, 128]; in 32-bit halves: the low 24 bits give q_5..q_3
+                // and a carry into the high part, which gives q_2..q_0
+                const long long N = (c == i) ? 0 : fixed48(a, e);
+                if (c == i) dg[i] = a;
+                int x = int(uint32_t(N) & 0xFFFFFFu);
+#pragma unroll
+                for (int p = kSlices - 1; p >= 3; p--) {
+                    const int d = bal8(x);
+                    dig[v2][p] = small_int_f32bits(d);
+                    x = (x - d) >> 8;
+                }
+                int y = int(N >> 24) + x;
+#pragma unroll
+                for (int p = 2; p >= 1; p--) {
+                    const int d = bal8(y);
+                    dig[v2][p] = small_int_f32bits(d);
+                    y = (y - d) >> 8;
+                }
+                dig[v2][0] = small_int_f32bits(y);  // top digit, |y| <= 128
+                if (c / kBand == i / kBand) band[size_t(c) * kBand + (i % kBand)] = f64_to_f32_rn(a);
+            }
+            wbf[u >> 1] = hb[0] | (hb[1] << 16);
+#pragma unroll
+            for (int p = 0; p < kSlices; p++) wd[p][u >> 1] = pack_hi16(dig[0][p], dig[1][p]);
         }
-        As[off] = __int2bfloat16_rn(int(N));  // top digit, |N| <= 128
-        if (c / kBand == i / kBand) band[size_t(c) * kBand + (i % kBand)] = f64_to_f32_rn(a);
+        *reinterpret_cast<uint4 *>(Abf + off) = make_uint4(wbf[0], wbf[1], wbf[2], wbf[3]);
+#pragma unroll
+        for (int p = 0; p < kSlices; p++)
+            *reinterpret_cast<uint4 *>(As + p * slice + off) = make_uint4(wd[p][0], wd[p][1], wd[p][2], wd[p][3]);
+        if (fp8) *reinterpret_cast<uint2 *>(A8 + off) = make_uint2(w8[0], w8[1]);
     }
 }
 
