@@ -176,6 +176,19 @@ __device__ __forceinline__ void load_vals(const View &v, int64_t i0, int64_t c0,
 {
     const int tid = threadIdx.x;
     const bool ci = contig_i(v);
+    if (c0 + 63 < i0 && i0 + 63 < v.k) {
+        // a tile strictly below the diagonal and inside the matrix: entry
+        // (fast, slow) sits at base + s fast + s lda slow (s = -1 reversed),
+        // with the contiguous index of A along fast
+        const int64_t x0 = ci ? i0 : c0, y0 = ci ? c0 : i0;
+        const int64_t sg = v.rev ? -1 : 1;
+        const int64_t base = v.rev ? (v.k - 1 - x0) + (v.k - 1 - y0) * v.lda : x0 + y0 * v.lda;
+        const double *p = v.A + base + sg * ((tid & 63) + int64_t(tid >> 6) * v.lda);
+        const int64_t step = 4 * sg * v.lda;
+#pragma unroll
+        for (int u = 0; u < 16; u++) val[u] = p[u * step];
+        return;
+    }
 #pragma unroll
     for (int u = 0; u < 16; u++) {
         const int fast = tid & 63, slow = (tid >> 6) + 4 * u;
@@ -789,8 +802,9 @@ slice_cols_kernel(const float *Y, int64_t kp, int64_t np, int64_t ncols, __nv_bf
         const int N = (be > 0) ? __float2int_rn(yi * up) : 0;
         const int q2 = ((N + 128) & 255) - 128;
         const int q1 = (N - q2) >> 8;
-        z1[i] = __int2bfloat16_rn(q1);
-        z2[i] = __int2bfloat16_rn(q2);
+        // |q1|, |q2| <= 128: the BF16 patterns are the top halves of the exact FP32 values
+        z1[i] = __ushort_as_bfloat16((unsigned short)(small_int_f32bits(q1) >> 16));
+        z2[i] = __ushort_as_bfloat16((unsigned short)(small_int_f32bits(q2) >> 16));
         const float d = float(N) * down;  // exact
         if (x) {
             const double dd = scaled_i32_to_f64(N, f - 16);  // the same value as a double
