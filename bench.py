@@ -335,7 +335,7 @@ def run_ours(args):
             B_pin.copy_(B_host0)
             api.trsm_mixed_host(side, uplo, trans, diag, alpha, A_pin, B_pin, tol=tol, prec=prec,
                                 max_iter=max_iter, stream=stream)
-    for _ in range(max(1, min(args.steps, 6))):
+    for _ in range(max(1, min(args.steps, 10))):
         B_pin.copy_(B_host0)  # fresh right-hand sides (host copy, not timed)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()

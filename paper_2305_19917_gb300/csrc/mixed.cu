@@ -709,34 +709,64 @@ writeback_kernel(double *B, int64_t ldb, bool left, bool rev, int64_t k, int64_t
 
 // Side = left: B's columns are the canonical columns (rows reversed for a
 // backward problem; X' 2^c_j as above), so no transpose: one column per CTA row of the grid,
-// each warp 128 rows, 4 lane-contiguous rows per thread (coalesced digit
-// loads and B stores); all 24 digit loads of a thread are issued before any
-// arithmetic, to keep enough bytes in flight.
+// each warp 128 rows, four consecutive rows per thread: one 8-byte load per
+// digit plane (or two 16-byte loads of X), and 16-byte stores of B when the
+// destination is aligned (scalar stores otherwise).
 __global__ void __launch_bounds__(256)
 writeback_left_kernel(double *B, int64_t ldb, bool rev, int64_t k, const double *X, int64_t kp, int64_t np,
                       const __nv_bfloat16 *Zs, const int *fz, int nz, const int *cs)
 {
     const int64_t j = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ib = (int64_t(blockIdx.y) * 8 + warp) * 128 + lane;
+    const int64_t ib = (int64_t(blockIdx.y) * 8 + warp) * 128 + 4 * lane;
+    if (ib >= k) return;  // ib < k <= kp, and kp is a multiple of 128: rows ib .. ib + 3 are in the buffers
     const size_t kn = size_t(kp) * size_t(np), o0 = size_t(ib) + size_t(j) * size_t(kp);
     const int cj = cs[j];
     double x[4];
     if (nz == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) x[q] = (ib + 32 * q < kp) ? unscale(X[o0 + 32 * q], cj) : 0.0;
+        const double2 a = *reinterpret_cast<const double2 *>(X + o0);
+        const double2 b = *reinterpret_cast<const double2 *>(X + o0 + 2);
+        x[0] = unscale(a.x, cj);
+        x[1] = unscale(a.y, cj);
+        x[2] = unscale(b.x, cj);
+        x[3] = unscale(b.y, cj);
     } else {
         const SlotCol c = slot_col(fz, nz, np, j, cj);
-        __nv_bfloat16 z[4][2 * kZSlots];
+        uint2 zz[2 * kZSlots];
 #pragma unroll
-        for (int q = 0; q < 4; q++) load_digits(z[q], Zs, nz, kn, o0 + 32 * q, ib + 32 * q < kp);
+        for (int u = 0; u < 2 * kZSlots; u++)
+            zz[u] = (u >> 1) < nz ? *reinterpret_cast<const uint2 *>(Zs + size_t(u >> 1) * 2 * kn + size_t(u & 1) * kn + o0)
+                                  : make_uint2(0u, 0u);
 #pragma unroll
-        for (int q = 0; q < 4; q++) x[q] = x_from_digits(z[q], nz, c);
+        for (int q = 0; q < 4; q++) {
+            __nv_bfloat16 z[2 * kZSlots];
+#pragma unroll
+            for (int u = 0; u < 2 * kZSlots; u++) {
+                const uint32_t w = (q < 2) ? zz[u].x : zz[u].y;
+                z[u] = __ushort_as_bfloat16((unsigned short)((q & 1) ? (w >> 16) : (w & 0xFFFFu)));
+            }
+            x[q] = x_from_digits(z, nz, c);
+        }
+    }
+    double *bc = B + j * ldb;
+    if (ib + 3 < k) {
+        // rows ib .. ib + 3 of X: B rows ib .. ib + 3, or k - 4 - ib .. k - 1 - ib reversed
+        double *d = rev ? bc + (k - 4 - ib) : bc + ib;
+        if ((reinterpret_cast<uintptr_t>(d) & 15) == 0) {
+            if (rev) {
+                reinterpret_cast<double2 *>(d)[0] = make_double2(x[3], x[2]);
+                reinterpret_cast<double2 *>(d)[1] = make_double2(x[1], x[0]);
+            } else {
+                reinterpret_cast<double2 *>(d)[0] = make_double2(x[0], x[1]);
+                reinterpret_cast<double2 *>(d)[1] = make_double2(x[2], x[3]);
+            }
+            return;
+        }
     }
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        const int64_t i = ib + 32 * q;
-        if (i < k) B[(rev ? k - 1 - i : i) + j * ldb] = x[q];
+        const int64_t i = ib + q;
+        if (i < k) bc[rev ? k - 1 - i : i] = x[q];
     }
 }
 
