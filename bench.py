@@ -713,6 +713,7 @@ def run_batched(args):
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
                 "config": {"workload": r["workload"], "units": r["units"], "grid": r["grid"], "tile": r["tile"],
+                           "tile_autotune_ms": r["tile_autotune_ms"],
                            "l2": f"B reset by one copy before each step; A+B pools exceed L2 ({r['pool_mb']:.0f} MB)"},
                 "roofline": r["roofline"], "cpu_baseline": r["cpu_baseline"], "e2e": r["e2e"],
                 "gpu_launches": r["launches"], "clocks": clk,

@@ -134,6 +134,25 @@ __device__ __forceinline__ void load_tile(const Unit<T> &u, int t, T *Tb)
     }
     const int j0 = jb * NBB, i0 = ib * NBB, k = u.k;
     const bool mt = u.flags & 1;
+    if (ib < jb && j0 + NBB <= k) {
+        // a gemm tile inside the triangle: entry (fast, slow) of the copy
+        // sits at base + s fast + s lda slow (s = -1 for a backward problem),
+        // fast running along A's contiguous dimension
+        const bool rev = u.flags & 2;
+        const int x0 = mt ? i0 : j0, y0 = mt ? j0 : i0;  // origin along the contiguous / strided index
+        const int64_t sg = rev ? -1 : 1;
+        const T *base = u.A + (rev ? int64_t(k - 1 - x0) + int64_t(k - 1 - y0) * u.lda : int64_t(x0) + int64_t(y0) * u.lda);
+        const int fast = threadIdx.x % NBB;
+        const T *p = base + sg * (fast + int64_t(threadIdx.x / NBB) * u.lda);
+        const int64_t step = sg * int64_t(NT / NBB) * u.lda;
+#pragma unroll
+        for (int q = 0; q < NBB * NBB / NT; q++) {
+            const int slow = threadIdx.x / NBB + q * (NT / NBB);
+            const int rr = mt ? slow : fast, kk = mt ? fast : slow;
+            cp_async_elem(Tb + kk * LT + rr, p + q * step, true);
+        }
+        return;
+    }
     for (int idx = threadIdx.x; idx < NBB * NBB; idx += NT) {
         const int fast = idx % NBB, slow = idx / NBB;
         const int rr = mt ? slow : fast, kk = mt ? fast : slow;
@@ -200,15 +219,22 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
         // rows k .. 32*nblk-1 are zero: the ragged last block multiplies them
         // by zero tile entries, and stale shared memory could hold a NaN
         const int kr = nblk * NBB;
-        for (int idx = tid; idx < kr * CW; idx += NT) {
-            int i, c;
-            if (left) { i = idx % kr; c = idx / kr; }   // contiguous along i
-            else      { c = idx % CW; i = idx / CW; }   // contiguous along c
-            const int io = rev ? k - 1 - i : i;
-            const bool in = c < cw && i < k;
-            cp_async_elem(Xs + i * LX + c, in ? (left ? u.B + io + int64_t(c) * u.ldb : u.B + c + int64_t(io) * u.ldb)
-                                              : u.B,
-                          in);
+        if (left) {
+            // contiguous along i: warp w takes columns w, w + 8, ..., its lanes the rows
+            for (int c = warp; c < CW; c += NT / 32) {
+                const T *bc = u.B + int64_t(c) * u.ldb;
+                for (int i = lane; i < kr; i += 32) {
+                    const bool in = c < cw && i < k;
+                    cp_async_elem(Xs + i * LX + c, in ? bc + (rev ? k - 1 - i : i) : u.B, in);
+                }
+            }
+        } else {
+            for (int idx = tid; idx < kr * CW; idx += NT) {  // contiguous along c (CW is a power of two)
+                const int c = idx % CW, i = idx / CW;
+                const int io = rev ? k - 1 - i : i;
+                const bool in = c < cw && i < k;
+                cp_async_elem(Xs + i * LX + c, in ? u.B + c + int64_t(io) * u.ldb : u.B, in);
+            }
         }
         cp_async_commit();
 #pragma unroll
@@ -320,15 +346,15 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
         cp_async_wait<0>();
 
         // ---- write back alpha * X (undo reversal / transposition) -----------
-        for (int idx = tid; idx < k * CW; idx += NT) {
-            int i, c;
-            if (left) { i = idx % k; c = idx / k; }
-            else      { c = idx % CW; i = idx / CW; }
-            if (c < cw) {
-                const int io = rev ? k - 1 - i : i;
-                const T v = u.alpha * Xs[i * LX + c];
-                if (left) u.B[io + int64_t(c) * u.ldb] = v;
-                else u.B[c + int64_t(io) * u.ldb] = v;
+        if (left) {
+            for (int c = warp; c < cw; c += NT / 32) {
+                T *bc = u.B + int64_t(c) * u.ldb;
+                for (int i = lane; i < k; i += 32) bc[rev ? k - 1 - i : i] = u.alpha * Xs[i * LX + c];
+            }
+        } else {
+            for (int idx = tid; idx < k * CW; idx += NT) {
+                const int c = idx % CW, i = idx / CW;
+                if (c < cw) u.B[c + int64_t(rev ? k - 1 - i : i) * u.ldb] = u.alpha * Xs[i * LX + c];
             }
         }
         __syncthreads();
