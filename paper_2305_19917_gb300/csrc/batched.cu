@@ -185,6 +185,35 @@ __device__ __forceinline__ void load_rows(const T *p, T (&a)[RR])
     }
 }
 
+// acc += (rows r .. r + RR - 1 of the k-major tile Tb) x (32 rows of X from
+// xr, columns cq ..), software-pipelined: the operands of step kk + 2 are
+// loaded while step kk multiplies (two warps per scheduler leave the
+// shared-memory latency exposed otherwise).
+template <typename T, int RR, int PER, int LX>
+__device__ __forceinline__ void tile_fma(T (&acc)[RR][PER], const T *Tb, const T *xr, int r, int cq)
+{
+    constexpr int D = 3;  // operand sets in registers (2 steps ahead)
+    T a[D][RR], x[D][PER];
+    auto load = [&](int kk, int b) {
+        load_rows<T, RR>(Tb + kk * LT + r, a[b]);
+        const uint4 xv = *reinterpret_cast<const uint4 *>(xr + kk * LX + cq);
+        const T *xp = reinterpret_cast<const T *>(&xv);
+#pragma unroll
+        for (int e = 0; e < PER; e++) x[b][e] = xp[e];
+    };
+    load(0, 0);
+    load(1, 1);
+#pragma unroll
+    for (int kk = 0; kk < NBB; kk++) {
+        if (kk + 2 < NBB) load(kk + 2, (kk + 2) % D);
+        const int b = kk % D;
+#pragma unroll
+        for (int q = 0; q < RR; q++)
+#pragma unroll
+            for (int e = 0; e < PER; e++) acc[q][e] += a[b][q] * x[b][e];
+    }
+}
+
 // smem: Xs[KMAX][LX], NBUF k-major tiles Ts[NBB][LT], inverse diagonal.
 template <typename T, int RR>
 __global__ void __launch_bounds__(NT)
@@ -262,18 +291,7 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
             const int j0 = jb * NBB, nr = min(NBB, k - j0);
             if (ib < jb) {
                 // gemm task: acc += Mv'(j, i) X_i
-                const int i0 = ib * NBB;
-#pragma unroll 8
-                for (int kk = 0; kk < NBB; kk++) {
-                    T a[RR];
-                    load_rows<T, RR>(Tb + kk * LT + r, a);
-                    const uint4 xv = *reinterpret_cast<const uint4 *>(Xs + (i0 + kk) * LX + cq);
-                    const T *x = reinterpret_cast<const T *>(&xv);
-#pragma unroll
-                    for (int q = 0; q < RR; q++)
-#pragma unroll
-                        for (int e = 0; e < PER; e++) acc[q][e] += a[q] * x[e];
-                }
+                tile_fma<T, RR, PER, LX>(acc, Tb, Xs + ib * NBB * LX, r, cq);
             } else if (u.Linv) {
                 // X_j -= sum of the gemm tasks, then the TS task as the
                 // product X_j = L_jj^-1 X_j on the register tiles
@@ -287,17 +305,7 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
                     for (int e = 0; e < PER; e++) acc[q][e] = T(0);
                 }
                 __syncthreads();
-#pragma unroll 8
-                for (int kk = 0; kk < NBB; kk++) {
-                    T a[RR];
-                    load_rows<T, RR>(Tb + kk * LT + r, a);
-                    const uint4 xv = *reinterpret_cast<const uint4 *>(Xs + (j0 + kk) * LX + cq);
-                    const T *x = reinterpret_cast<const T *>(&xv);
-#pragma unroll
-                    for (int q = 0; q < RR; q++)
-#pragma unroll
-                        for (int e = 0; e < PER; e++) acc[q][e] += a[q] * x[e];
-                }
+                tile_fma<T, RR, PER, LX>(acc, Tb, Xs + j0 * LX, r, cq);
                 __syncthreads();  // every thread has read X_j
 #pragma unroll
                 for (int q = 0; q < RR; q++) {
