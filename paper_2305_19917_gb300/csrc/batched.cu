@@ -279,12 +279,13 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
 #pragma unroll
             for (int e = 0; e < PER; e++) acc[a][e] = T(0);
         for (int tt = 0; tt < ntile; tt++) {
-            // keep NBUF - 1 tiles in flight: issue tile tt + NBUF - 1, then
-            // wait until tile tt (and the B chunk) has landed
+            // wait until tile tt (and the B chunk) has landed; the barrier
+            // also means every thread is done with tile tt - 1, whose buffer
+            // then takes tile tt + NBUF - 1 (NBUF - 1 tiles stay in flight)
+            cp_async_wait<NBUF - 2>();
+            __syncthreads();
             if (tt + NBUF - 1 < ntile) load_tile(u, tt + NBUF - 1, Ts + ((tt + NBUF - 1) % NBUF) * TS);
             cp_async_commit();
-            cp_async_wait<NBUF - 1>();
-            __syncthreads();
             const T *Tb = Ts + (tt % NBUF) * TS;
             int jb, ib;
             tile_of(tt, jb, ib);
@@ -349,9 +350,9 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
                     for (int e = 0; e < CPW; e++) Xs[(j0 + lane) * LX + warp + 8 * e] = tv[e];
                 }
             }
-            __syncthreads();  // the buffer of tile tt is reused NBUF - 1 tiles later
         }
         cp_async_wait<0>();
+        __syncthreads();  // the last block's X (written by every thread) is complete
 
         // ---- write back alpha * X (undo reversal / transposition) -----------
         if (left) {
