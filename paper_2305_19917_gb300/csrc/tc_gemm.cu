@@ -496,7 +496,11 @@ int launch_tc_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t 
     if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return GB_STATUS_CUDA_ERROR;
     const int64_t mt = (M + BM - 1) / BM;
     const int64_t sms = num_sms() > 0 ? num_sms() : 152;
-    if (mt * ((N + 255) / 256) >= 2 * sms)
+    // fraction of the last round of tiles that is filled, over all rounds
+    auto wave_eff = [&](int64_t tiles) { return double(tiles) / double((tiles + sms - 1) / sms * sms); };
+    const int64_t t256 = mt * ((N + 255) / 256), t128 = mt * ((N + 127) / 128);
+    // the 256-wide tile unless the 128-wide one fills the rounds markedly better
+    if (t256 >= 2 * sms && !(wave_eff(t128) > wave_eff(t256) + 0.1))
         return launch_persistent<256>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
     if (mt * ((N + 127) / 128) >= 2 * sms)
         return launch_persistent<128>(M, N, K, A, lda, B, ldb, C, ldc, alpha, s, status);
