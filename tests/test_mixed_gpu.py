@@ -40,6 +40,32 @@ def test_mixed_all_forms(side, uplo, trans, diag):
     assert fwd_err(X, Xo) <= 1e-10
 
 
+@pytest.mark.parametrize("side,uplo,trans,diag,m,n,ldpad", [
+    (0, 0, 0, 0, 300, 170, 3), (0, 1, 0, 0, 257, 130, 1), (0, 0, 1, 1, 384, 64, 5), (1, 1, 1, 0, 140, 333, 3)])
+def test_mixed_padded_leading_dimensions(side, uplo, trans, diag, m, n, ldpad):
+    """B inside a buffer with ldb = m + ldpad (odd paddings, so the columns
+    change their 16-byte alignment one to the next) and A with lda = k + 2:
+    the solution matches the oracle and nothing outside the m x n matrix
+    (canaries in the padding rows) is written."""
+    import torch
+    from paper_2305_19917_gb300 import api
+    A, B = inputs.make_problem(side, uplo, trans, diag, m, n, seed=31 + m)
+    Xo = oracle.dtrsm(side, uplo, trans, diag, 1.5, A, B)
+    k = A.shape[0]
+    abuf = torch.full((k, k + 2), 7.0, dtype=torch.float64, device="cuda").t()
+    Ad = abuf[:k, :k]
+    Ad.copy_(torch.as_tensor(A))
+    canary = 1234.5
+    bbuf = torch.full((n, m + ldpad), canary, dtype=torch.float64, device="cuda").t()
+    Bd = bbuf[:m, :n]
+    Bd.copy_(torch.as_tensor(B))
+    st, it, est = api.trsm_mixed(side, uplo, trans, diag, 1.5, Ad, Bd, tol=1e-11)
+    torch.cuda.synchronize()
+    assert st == 0, (st, it, est)
+    assert fwd_err(Bd.cpu().numpy(), Xo) <= 1e-10
+    assert bool(torch.all(bbuf[m:, :n] == canary).item())
+
+
 @pytest.mark.parametrize("m,n", [(1, 1), (2, 300), (129, 7), (512, 512), (700, 129)])
 def test_mixed_ragged_sizes(m, n):
     A, B = inputs.make_problem(0, 0, 0, 0, m, n, seed=m + n)
