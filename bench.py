@@ -452,6 +452,7 @@ def run_extras(stream, rank):
     """The other configurations, timed briefly on the same GPU (device-
     resident inputs, CUDA events, B reset outside the events):
       * mixed FP8 E4M3 (per-block power-of-two scales) at m = n = 16384;
+      * mixed BF16 at m = n = 16384 on two more seeds (the headline's is 0);
       * mixed BF16 and FP8 at m = 32768, n = 4096, with plain FP64 beside them;
       * plain FP64 at m = n = 8192 in all 16 side/uplo/trans/diag forms and at
         m = n = 16384 in two more forms (Right/Upper/T/Unit, Left/Upper/T/NonUnit),
@@ -514,6 +515,11 @@ def run_extras(stream, rank):
     A, B0 = inputs.make_problem_device(0, 0, 0, 0, 16384, 16384, seed=0)
     mixed_leg("mixed_fp8_16384", A, B0, "fp8", "device generator seed 0")
     del A, B0
+    # the headline configuration (BF16, 16384^2) on two more seeds
+    for sd in (1, 2):
+        A, B0 = inputs.make_problem_device(0, 0, 0, 0, 16384, 16384, seed=sd)
+        mixed_leg(f"mixed_bf16_16384_seed{sd}", A, B0, "bf16", f"device generator seed {sd}")
+        del A, B0
     # 32768 x 4096: BF16, FP8 and plain FP64
     A, B0 = inputs.make_problem_device(0, 0, 0, 0, 32768, 4096, seed=1)
     mixed_leg("mixed_bf16_32768x4096", A, B0, "bf16", "device generator seed 1")
