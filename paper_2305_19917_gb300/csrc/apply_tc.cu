@@ -157,11 +157,12 @@ leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const uint32_t phs = (gi / LST) & 1u;
                 if (!tc::mbar_wait(&full[st], phs, ab, status, tc::TC_TIMEOUT_MMA)) break;
                 tc::tc_fence_after();
-                const uint32_t a0 = tc::smem_u32(ring + st * LSTAGE), x0 = a0 + LA_BYTES;
+                // descriptors in 16-byte units: a 32-byte K step adds 2
+                const uint32_t a0 = tc::smem_u32(ring + st * LSTAGE);
+                const uint64_t da = tc::desc_kmajor_sw128(a0), dx = tc::desc_kmajor_sw128(a0 + LA_BYTES);
+                tc::mma_f16(tmem, da, dx, idesc, kt != 0);
 #pragma unroll
-                for (int kk = 0; kk < 4; kk++)
-                    tc::mma_f16(tmem, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(x0 + kk * 32), idesc,
-                                (kt | kk) != 0);
+                for (int kk = 1; kk < 4; kk++) tc::mma_f16(tmem, da + uint64_t(2 * kk), dx + uint64_t(2 * kk), idesc, 1);
                 tc::mma_commit(&empty[st]);
             }
             tc::mma_commit(&bar_g);  // also when nk == 0: arrives once the earlier MMAs are done
@@ -213,12 +214,12 @@ leaf_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 uint32_t acc = 0;
 #pragma unroll
                 for (int pr = 0; pr < 3; pr++) {
-                    const uint32_t a0 = tc::smem_u32(As[pr]), y0 = tc::smem_u32(Bs[pr]);
+                    const uint64_t da = tc::desc_kmajor_sw128(tc::smem_u32(As[pr]));
+                    const uint64_t dy = tc::desc_kmajor_sw128(tc::smem_u32(Bs[pr]));
 #pragma unroll
                     for (int kk = 0; kk < TB / 16; kk++) {
-                        const uint32_t o = uint32_t(kk >> 2) * HALF_BYTES + uint32_t(kk & 3) * 32u;
-                        tc::mma_f16(tmem + TB, tc::desc_kmajor_sw128(a0 + o), tc::desc_kmajor_sw128(y0 + o), idesc,
-                                    acc);
+                        const uint64_t o = uint64_t(((kk >> 2) * HALF_BYTES + (kk & 3) * 32u) >> 4);
+                        tc::mma_f16(tmem + TB, da + o, dy + o, idesc, acc);
                         acc = 1;
                     }
                 }

@@ -151,18 +151,18 @@ tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            // descriptors from the ring's base ones (16-byte units: a 32-byte K step adds 2)
+            const uint64_t dA0 = tc::desc_kmajor_sw128(tc::smem_u32(sA)), dB0 = tc::desc_kmajor_sw128(tc::smem_u32(sB));
             for (int kt = 0; kt < nk; kt++) {
                 const int s = kt % STAGES;
                 const uint32_t ph = (kt / STAGES) & 1;
                 if (!tc::mbar_wait(&full[s], ph, ab, status, tc::TC_TIMEOUT_MMA)) break;
                 tc::tc_fence_after();
-                const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
-                const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
+                const uint64_t da = dA0 + uint64_t(uint32_t(s) * (A_BYTES >> 4));
+                const uint64_t db = dB0 + uint64_t(uint32_t(s) * (B_BYTES >> 4));
+                tc::mma_f16(tmem, da, db, idesc, kt != 0);
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; kk++) {
-                    tc::mma_f16(tmem, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
-                                idesc, (kt | kk) != 0);
-                }
+                for (int kk = 1; kk < BK / 16; kk++) tc::mma_f16(tmem, da + uint64_t(2 * kk), db + uint64_t(2 * kk), idesc, 1);
                 tc::mma_commit(&empty[s]);
             }
             tc::mma_commit(accf);
@@ -309,7 +309,11 @@ tc_gemm_bf16_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, PBN);
-            uint32_t kg = 0;
+            // descriptors from the ring's base ones (16-byte units: a 32-byte K step adds
+            // 2), and the ring position kept incrementally (no division per K step)
+            const uint64_t dA0 = tc::desc_kmajor_sw128(tc::smem_u32(sA)), dB0 = tc::desc_kmajor_sw128(tc::smem_u32(sB));
+            int s = 0;
+            uint32_t ph = 0;
             int it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, it++) {
@@ -318,21 +322,22 @@ tc_gemm_bf16_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __
                 if (!tc::mbar_wait(&tempty[buf], (use & 1) ^ 1, ab, status, tc::TC_TIMEOUT_MMA)) break;
                 tc::tc_fence_after();
                 const uint32_t d = tmem + uint32_t(buf * PBN);
-                for (int kt = 0; kt < nk; kt++, kg++) {
-                    const int s = kg % PSTAGES;
-                    const uint32_t ph = (kg / PSTAGES) & 1;
+                for (int kt = 0; kt < nk; kt++) {
                     if (!tc::mbar_wait(&full[s], ph, ab, status, tc::TC_TIMEOUT_MMA)) {
                         ok = false;
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
-                    const uint32_t b0 = tc::smem_u32(sB + s * P_B_BYTES);
+                    const uint64_t da = dA0 + uint64_t(uint32_t(s) * (A_BYTES >> 4));
+                    const uint64_t db = dB0 + uint64_t(uint32_t(s) * (P_B_BYTES >> 4));
+                    tc::mma_f16(d, da, db, idesc, kt != 0);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; kk++)
-                        tc::mma_f16(d, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
-                                    idesc, (kt | kk) != 0);
+                    for (int kk = 1; kk < BK / 16; kk++) tc::mma_f16(d, da + uint64_t(2 * kk), db + uint64_t(2 * kk), idesc, 1);
                     tc::mma_commit(&empty[s]);
+                    if (++s == PSTAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (ok) tc::mma_commit(&tfull[buf]);
             }

@@ -83,6 +83,8 @@ tc_gemm_fp8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_e4m3_f32(BM, BN);
+            // descriptors from the ring's base ones (16-byte units: a 32-byte K step adds 2)
+            const uint64_t dA0 = tc::desc_kmajor_sw128(tc::smem_u32(sAm)), dB0 = tc::desc_kmajor_sw128(tc::smem_u32(sBm));
             for (int kt = 0; kt < nk; kt++) {
                 const int s = kt % STAGES;
                 const uint32_t ph = (kt / STAGES) & 1;
@@ -90,12 +92,11 @@ tc_gemm_fp8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 if (!tc::mbar_wait(&acce[buf], ((kt >> 1) & 1) ^ 1, ab, status, tc::TC_TIMEOUT_MMA)) break;
                 if (!tc::mbar_wait(&full[s], ph, ab, status, tc::TC_TIMEOUT_MMA)) break;
                 tc::tc_fence_after();
-                const uint32_t a0 = tc::smem_u32(sAm + s * A_BYTES);
-                const uint32_t b0 = tc::smem_u32(sBm + s * B_BYTES);
+                const uint64_t da = dA0 + uint64_t(uint32_t(s) * (A_BYTES >> 4));
+                const uint64_t db = dB0 + uint64_t(uint32_t(s) * (B_BYTES >> 4));
 #pragma unroll
                 for (int kk = 0; kk < BK / 32; kk++)
-                    tc::mma_f8(tmem + uint32_t(buf * BN), tc::desc_kmajor_sw128(a0 + kk * 32),
-                               tc::desc_kmajor_sw128(b0 + kk * 32), idesc, kk != 0);
+                    tc::mma_f8(tmem + uint32_t(buf * BN), da + uint64_t(2 * kk), db + uint64_t(2 * kk), idesc, kk != 0);
                 tc::mma_commit(&empty[s]);
                 tc::mma_commit(&accf[buf]);
             }

@@ -132,6 +132,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            const uint64_t dA0 = tc::desc_kmajor_sw128(tc::smem_u32(sA)), dB0 = tc::desc_kmajor_sw128(tc::smem_u32(sB));
             int g = 0;
             for (int cp = 0; cp < npass; cp++) {
                 const int c = cp / P, p = cp % P;
@@ -153,12 +154,16 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
-                    const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
+                    // the stage's descriptors from the ring's base ones: the start
+                    // address field counts 16-byte units, so a 32-byte step along
+                    // K adds 2 (few instructions per MMA: the one-slice passes
+                    // issue an N = 128 MMA every 64 tensor-core clocks)
+                    const uint64_t da = dA0 + uint64_t(uint32_t(s) * (A_BYTES >> 4));
+                    const uint64_t db = dB0 + uint64_t(uint32_t(s) * (B_BYTES >> 4));
+                    tc::mma_f16(d, da, db, idesc, kt != 0);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; kk++)
-                        tc::mma_f16(d, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
-                                    idesc, (kt | kk) != 0);
+                    for (int kk = 1; kk < BK / 16; kk++)
+                        tc::mma_f16(d, da + uint64_t(2 * kk), db + uint64_t(2 * kk), idesc, 1);
                     tc::mma_commit(&empty[s]);
                 }
                 tc::mma_commit(&accf[buf]);
