@@ -27,7 +27,19 @@
 // per CTA and K step: 16 KB of A plus 32 or 16 KB of Z).  Pass p multiplies
 // slice a_p with [z_1; z_2] (256 x 64, z_2 only in passes p < P2) into one of
 // two 128 x 256 TMEM accumulators, so that draining pass p overlaps the MMAs
-// of pass p+1.  Warp 0: TMA, warp 1: TMEM + MMA issue, warps 2-9: epilogue
+// of pass p+1.  A pass of one slice with z_1 alone needs 32 KB of operands
+// per 256 tensor-core clocks, more than the L2 delivers to an SM; so when
+// P2 = P - 1 <= 2 (the pairs (P-1, 2) and (P, 1) have the same weight) the
+// last two slices share one pass: per K step a_(P-1) [z_1; z_2] and a_P z_1, the
+// latter added into the z_2 half of the accumulator.  The K step takes two
+// ring entries, slice P-1 with both z tiles, then slice P with its own copy
+// of z_1 (80 KB per 768 clocks): each entry is released when its own MMAs
+// are done, so the ring keeps its lookahead (with z_1 read from the first
+// entry only, both stayed held until the second was done, and the pass ran
+// slower than the separate passes).  Two products in one accumulator need
+// its K range halved to 512 to keep every sum within 2^24, so such a pass
+// runs as two half-chunk passes.
+// Warp 0: TMA, warp 1: TMEM + MMA issue, warps 2-9: epilogue
 // (warp w drains TMEM lanes 32*(w%4).., column half (w-2)/4).  Tiles are
 // rasterised in groups of 8 row tiles, longest K ranges (lowest rows) first.
 #include "common.cuh"
@@ -48,6 +60,30 @@ constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr size_t SMEM_BYTES = 1024 + STAGES * size_t(STAGE_BYTES) + 256;
 constexpr int NTHREADS = 320;
 constexpr int kRasterGroup = 8;
+// exactness needs K <= 1024 per tensor-memory accumulation of one product
+// (1024 x 2^14 = 2^24), K <= 512 where two products share an accumulator
+constexpr int KC = 1024;
+
+// One pass of a K chunk: A slice p (0-based) times z_1 (and z_2 if nsl = 2)
+// over K in [kb, ke); a merged pass also multiplies slice p + 1 with z_1.
+struct Pass {
+    int p, nsl, kb, ke;
+    bool merged;
+};
+
+// Passes of the chunk [kc0, kc1): slices 0..P-1 one pass each, or with
+// merging, slices 0..P-3 and then the merged pair P-2, P-1 over the chunk's
+// two halves (one if the chunk is at most 512 long).
+__device__ __forceinline__ int chunk_passes(int kc0, int kc1, int P, bool merge)
+{
+    return merge ? P - 1 + (kc1 - kc0 > KC / 2 ? 1 : 0) : P;
+}
+__device__ __forceinline__ Pass chunk_pass(int j, int kc0, int kc1, int P, int P2, bool merge)
+{
+    if (!merge || j < P - 2) return Pass{j, j < P2 ? 2 : 1, kc0, kc1, false};
+    const int mid = min(kc0 + KC / 2, kc1);
+    return j == P - 2 ? Pass{P - 2, 2, kc0, mid, true} : Pass{P - 2, 2, mid, kc1, true};
+}
 
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmZ,
@@ -73,12 +109,14 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const int i0 = m_blk * BM, j0 = n_blk * BNO;
     const int k_end = min(k_hi, i0 + BM);  // this tile's K range is [k_lo, k_end)
     if (k_end <= k_lo) return;             // the tile lies entirely above the diagonal
-    // exactness needs K <= 1024 per tensor-memory accumulation: the K range
-    // is cut into chunks of at most 1024, each pass of each chunk drained
-    // separately into the same int64 sums
-    constexpr int KC = 1024;
+    // the K range is cut into chunks of at most 1024, each pass of each
+    // chunk drained separately into the same int64 sums
     const int nchunks = (k_end - k_lo + KC - 1) / KC;
-    const int npass = nchunks * P;
+    // merged only up to P = 3: at P = 5 (the first residual, K = 16384) the
+    // merged pass gained no time and read 1.8x the DRAM bytes of the
+    // separate passes (35 against 19 GB), at P = 3 it was 4 % faster with
+    // the same DRAM bytes
+    const bool merge = P >= 2 && P <= 3 && P2 == P - 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -105,21 +143,27 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             tc::tma_prefetch_desc(&tmZ);
             int g = 0;
             bool ok = true;
-            for (int cp = 0; cp < npass && ok; cp++) {
-                const int c = cp / P, p = cp % P;
-                const int nsl = p < P2 ? 2 : 1;
+            // one ring entry: slice p's A tile and the first nsl z tiles
+            auto load = [&](int kk, int p, int nsl) {
+                const int s = g % STAGES;
+                const uint32_t ph = (g / STAGES) & 1;
+                if (!tc::mbar_wait(&empty[s], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) return false;
+                tc::mbar_arrive_expect_tx(&full[s], A_BYTES + uint32_t(nsl) * ZS_BYTES);
+                tc::tma_load_3d(&tmA, &full[s], sA + s * A_BYTES, kk, i0, p);
+                for (int q = 0; q < nsl; q++)
+                    tc::tma_load_3d(&tmZ, &full[s], sB + s * B_BYTES + q * ZS_BYTES, kk, j0, q);
+                g++;
+                return true;
+            };
+            for (int c = 0; c < nchunks && ok; c++) {
                 const int kc0 = k_lo + c * KC, kc1 = min(kc0 + KC, k_end);
-                for (int kk = kc0; kk < kc1; kk += BK, g++) {
-                    const int s = g % STAGES;
-                    const uint32_t ph = (g / STAGES) & 1;
-                    if (!tc::mbar_wait(&empty[s], ph ^ 1, ab, status, tc::TC_TIMEOUT_PRODUCER)) {
-                        ok = false;
-                        break;
+                const int nj = chunk_passes(kc0, kc1, P, merge);
+                for (int j = 0; j < nj && ok; j++) {
+                    const Pass ps = chunk_pass(j, kc0, kc1, P, P2, merge);
+                    for (int kk = ps.kb; kk < ps.ke && ok; kk += BK) {
+                        ok = load(kk, ps.p, ps.nsl);
+                        if (ok && ps.merged) ok = load(kk, ps.p + 1, 1);
                     }
-                    tc::mbar_arrive_expect_tx(&full[s], A_BYTES + uint32_t(nsl) * ZS_BYTES);
-                    tc::tma_load_3d(&tmA, &full[s], sA + s * A_BYTES, kk, i0, p);
-                    for (int q = 0; q < nsl; q++)
-                        tc::tma_load_3d(&tmZ, &full[s], sB + s * B_BYTES + q * ZS_BYTES, kk, j0, q);
                 }
             }
             // tail: wait until the MMAs released every stage, so that no
@@ -133,41 +177,63 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     } else if (warp == 1) {
         if (lane == 0) {
             const uint64_t dA0 = tc::desc_kmajor_sw128(tc::smem_u32(sA)), dB0 = tc::desc_kmajor_sw128(tc::smem_u32(sB));
-            int g = 0;
-            for (int cp = 0; cp < npass; cp++) {
-                const int c = cp / P, p = cp % P;
-                const int kc0 = k_lo + c * KC;
-                const int nk = (min(kc0 + KC, k_end) - kc0) / BK;
-                const int buf = cp & 1;
-                const uint32_t use = cp >> 1;
-                if (!tc::mbar_wait(&acce[buf], (use & 1) ^ 1, ab, status, tc::TC_TIMEOUT_MMA)) break;
+            const uint32_t idesc256 = tc::idesc_bf16_f32(BM, 256), idesc128 = tc::idesc_bf16_f32(BM, 128);
+            int g = 0, cp = 0;
+            bool ok = true;
+            // ring entry g: wait until its copies landed, return its stage
+            auto take = [&](int &s) {
+                s = g % STAGES;
+                const uint32_t ph = (g / STAGES) & 1;
+                g++;
+                if (!tc::mbar_wait(&full[s], ph, ab, status, tc::TC_TIMEOUT_MMA)) return false;
                 tc::tc_fence_after();
-                const bool two = p < P2;  // pair (p+1, 2) formed
-                const uint32_t idesc = two ? tc::idesc_bf16_f32(BM, 256) : tc::idesc_bf16_f32(BM, 128);
-                const uint32_t d = tmem + uint32_t(buf * 256);
-                bool ok = true;
-                for (int kt = 0; kt < nk; kt++, g++) {
-                    const int s = g % STAGES;
-                    const uint32_t ph = (g / STAGES) & 1;
-                    if (!tc::mbar_wait(&full[s], ph, ab, status, tc::TC_TIMEOUT_MMA)) {
+                return true;
+            };
+            for (int c = 0; c < nchunks && ok; c++) {
+                const int kc0 = k_lo + c * KC, kc1 = min(kc0 + KC, k_end);
+                const int nj = chunk_passes(kc0, kc1, P, merge);
+                for (int j = 0; j < nj && ok; j++, cp++) {
+                    const Pass ps = chunk_pass(j, kc0, kc1, P, P2, merge);
+                    const int nk = (ps.ke - ps.kb) / BK;
+                    const int buf = cp & 1;
+                    const uint32_t use = cp >> 1;
+                    if (!tc::mbar_wait(&acce[buf], (use & 1) ^ 1, ab, status, tc::TC_TIMEOUT_MMA)) {
                         ok = false;
                         break;
                     }
                     tc::tc_fence_after();
-                    // the stage's descriptors from the ring's base ones: the start
-                    // address field counts 16-byte units, so a 32-byte step along
-                    // K adds 2 (few instructions per MMA: the one-slice passes
-                    // issue an N = 128 MMA every 64 tensor-core clocks)
-                    const uint64_t da = dA0 + uint64_t(uint32_t(s) * (A_BYTES >> 4));
-                    const uint64_t db = dB0 + uint64_t(uint32_t(s) * (B_BYTES >> 4));
-                    tc::mma_f16(d, da, db, idesc, kt != 0);
+                    // pair (p+1, 2) formed: one N = 256 MMA over [z_1; z_2]
+                    const uint32_t idesc = ps.nsl == 2 ? idesc256 : idesc128;
+                    const uint32_t d = tmem + uint32_t(buf * 256);
+                    for (int kt = 0; kt < nk; kt++) {
+                        int s;
+                        if (!(ok = take(s))) break;
+                        // the stage's descriptors from the ring's base ones: the start
+                        // address field counts 16-byte units, so a 32-byte step along
+                        // K adds 2 (few instructions per MMA: an N = 128 MMA takes
+                        // 64 tensor-core clocks)
+                        const uint64_t da = dA0 + uint64_t(uint32_t(s) * (A_BYTES >> 4));
+                        const uint64_t db = dB0 + uint64_t(uint32_t(s) * (B_BYTES >> 4));
+                        tc::mma_f16(d, da, db, idesc, kt != 0);
 #pragma unroll
-                    for (int kk = 1; kk < BK / 16; kk++)
-                        tc::mma_f16(d, da + uint64_t(2 * kk), db + uint64_t(2 * kk), idesc, 1);
-                    tc::mma_commit(&empty[s]);
+                        for (int kk = 1; kk < BK / 16; kk++)
+                            tc::mma_f16(d, da + uint64_t(2 * kk), db + uint64_t(2 * kk), idesc, 1);
+                        tc::mma_commit(&empty[s]);
+                        if (ps.merged) {
+                            // slice p+2 (1-based) times its own copy of z_1, added
+                            // into the z_2 half (the same pair weight)
+                            int s2;
+                            if (!(ok = take(s2))) break;
+                            const uint64_t da2 = dA0 + uint64_t(uint32_t(s2) * (A_BYTES >> 4));
+                            const uint64_t db2 = dB0 + uint64_t(uint32_t(s2) * (B_BYTES >> 4));
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; kk++)
+                                tc::mma_f16(d + 128u, da2 + uint64_t(2 * kk), db2 + uint64_t(2 * kk), idesc128, 1);
+                            tc::mma_commit(&empty[s2]);
+                        }
+                    }
+                    tc::mma_commit(&accf[buf]);
                 }
-                tc::mma_commit(&accf[buf]);
-                if (!ok) break;
             }
         }
     } else {
@@ -178,8 +244,13 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
         for (int c = 0; c < 64; c++) T[c] = 0;
         bool ok = true;
-        for (int cp = 0; cp < npass; cp++) {
-            const int p = cp % P;
+        int cp = 0;
+        for (int c = 0; c < nchunks && ok; c++) {
+          const int kc0 = k_lo + c * KC, kc1 = min(kc0 + KC, k_end);
+          const int nj = chunk_passes(kc0, kc1, P, merge);
+          for (int jp = 0; jp < nj; jp++, cp++) {
+            const Pass ps = chunk_pass(jp, kc0, kc1, P, P2, merge);
+            const int p = ps.p;
             const int buf = cp & 1;
             const uint32_t use = cp >> 1;
             if (!tc::mbar_wait(&accf[buf], use & 1, ab, status, tc::TC_TIMEOUT_EPILOGUE)) {
@@ -187,7 +258,9 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 break;
             }
             tc::tc_fence_after();
-            const bool two = p < P2;
+            // the z_2 half holds pair (p+1, 2), and in a merged pass also
+            // (p+2, 1): both of weight 2^-(8p+24)
+            const bool two = ps.nsl == 2;
             const int s1 = W - (8 * (p + 1) + 8);
             const int s2 = W - (8 * (p + 1) + 16);
             const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 256 + half * 64);
@@ -211,6 +284,7 @@ tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acce[buf]);
+          }
         }
         if (ok) {
             // the exact sums of this tile: lanes hold consecutive rows, so
