@@ -17,10 +17,14 @@
 // Tile shapes (the autotuner's choice, gb_batched_autotune): in the gemm
 // tasks each thread owns RR rows x one 16-byte vector of right-hand sides
 // (PER = 2 FP64 / 4 FP32 columns), so a unit is CW = 8 PER RR right-hand
-// sides wide: RR = 1 gives 16 (FP64) / 32 (FP32) columns and three CTAs per
-// SM; RR = 2 gives 32 / 64 columns, twice the multiply-adds per shared-memory
-// load, one CTA per SM.  A tiles are stored k-major so that a thread's RR
-// rows load as one vector.
+// sides wide: RR = 1 gives 16 (FP64) / 32 (FP32) columns and two CTAs per
+// SM (109 KB of shared memory each); RR = 2 gives 32 / 64 columns, twice the
+// multiply-adds per shared-memory load, one CTA per SM.  A tiles are stored
+// k-major so that a thread's RR rows load as one vector.  A warp owns a few
+// whole columns of the block (its lanes the rows), so a step's A rows load
+// as whole wavefronts and its X vector as a broadcast, and the warps whose
+// columns lie past the last right-hand side of a chunk skip their products
+// (a chunk is often narrower than CW: the last one of every instance).
 //
 // FP32 solves the 32 x 32 diagonal blocks with their inverses: a first kernel
 // of the plan's graph inverts every diagonal block of every instance once per
@@ -100,26 +104,28 @@ __device__ __forceinline__ const T *mv_addr(const Unit<T> &u, int i, int j)
     return mt ? u.A + jo + int64_t(io) * u.lda : u.A + io + int64_t(jo) * u.lda;
 }
 
-// Tile number t of a unit's sequence: block row jb, then tiles ib = 0..jb
-// (ib < jb: gemm tasks, ib == jb: the TS task), i.e. t = jb(jb+1)/2 + ib.
-__device__ __forceinline__ void tile_of(int t, int &jb, int &ib)
-{
-    int j = int((sqrtf(8.0f * float(t) + 1.0f) - 1.0f) * 0.5f);
-    while ((j + 1) * (j + 2) / 2 <= t) j++;
-    while (j * (j + 1) / 2 > t) j--;
-    jb = j;
-    ib = t - j * (j + 1) / 2;
-}
+// A unit's tiles in sequence: block row jb, then tiles ib = 0..jb (ib < jb:
+// gemm tasks, ib == jb: the TS task); the position steps along the sequence.
+struct TilePos {
+    int jb = 0, ib = 0;
+    __device__ __forceinline__ void next()
+    {
+        if (ib == jb) {
+            jb++;
+            ib = 0;
+        } else {
+            ib++;
+        }
+    }
+};
 
-// Issue the asynchronous loads of tile t into buffer Tb (reading along A's
-// contiguous dimension): the gemm tiles in full, the TS tile on and below
-// its diagonal; everything else (and the ragged edge) reads as zero.  Tb is
-// k-major: Tb[kk * LT + rr] = Mv'(j0 + rr, i0 + kk).
+// Issue the asynchronous loads of tile (jb, ib) into buffer Tb (reading
+// along A's contiguous dimension): the gemm tiles in full, the TS tile on
+// and below its diagonal; everything else (and the ragged edge) reads as
+// zero.  Tb is k-major: Tb[kk * LT + rr] = Mv'(j0 + rr, i0 + kk).
 template <typename T>
-__device__ __forceinline__ void load_tile(const Unit<T> &u, int t, T *Tb)
+__device__ __forceinline__ void load_tile(const Unit<T> &u, int jb, int ib, T *Tb)
 {
-    int jb, ib;
-    tile_of(t, jb, ib);
     if (u.Linv && ib == jb) {
         // the TS task's tile: the block's precomputed inverse (k-major 32 x
         // 32 in global memory), in 8-byte pieces into the LT-strided layout
@@ -266,33 +272,45 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
             }
         }
         cp_async_commit();
-#pragma unroll
+        TilePos pf;  // the next tile to load
+#pragma unroll 1
         for (int q = 0; q < NBUF - 1; q++) {
-            if (q < ntile) load_tile(u, q, Ts + q * TS);
+            if (q < ntile) {
+                load_tile(u, pf.jb, pf.ib, Ts + q * TS);
+                pf.next();
+            }
             cp_async_commit();
         }
 
-        const int r = (tid / C::COLG) * RR, cq = (tid % C::COLG) * PER;
+        // a warp owns PER * 32 / ROWG columns of every row of the block, so
+        // its A rows load as whole wavefronts and its X vector as a
+        // broadcast, and a warp past the chunk's last right-hand side skips
+        // its products (the columns of X there stay zero)
+        const int r = (tid % C::ROWG) * RR, cq = (tid / C::ROWG) * PER;
+        const bool live = cq < cw;
         T acc[RR][PER];
 #pragma unroll
         for (int a = 0; a < RR; a++)
 #pragma unroll
             for (int e = 0; e < PER; e++) acc[a][e] = T(0);
-        for (int tt = 0; tt < ntile; tt++) {
+        TilePos cur;  // tile tt
+        for (int tt = 0; tt < ntile; tt++, cur.next()) {
             // wait until tile tt (and the B chunk) has landed; the barrier
             // also means every thread is done with tile tt - 1, whose buffer
             // then takes tile tt + NBUF - 1 (NBUF - 1 tiles stay in flight)
             cp_async_wait<NBUF - 2>();
             __syncthreads();
-            if (tt + NBUF - 1 < ntile) load_tile(u, tt + NBUF - 1, Ts + ((tt + NBUF - 1) % NBUF) * TS);
+            if (tt + NBUF - 1 < ntile) {
+                load_tile(u, pf.jb, pf.ib, Ts + ((tt + NBUF - 1) % NBUF) * TS);
+                pf.next();
+            }
             cp_async_commit();
             const T *Tb = Ts + (tt % NBUF) * TS;
-            int jb, ib;
-            tile_of(tt, jb, ib);
+            const int jb = cur.jb, ib = cur.ib;
             const int j0 = jb * NBB, nr = min(NBB, k - j0);
             if (ib < jb) {
                 // gemm task: acc += Mv'(j, i) X_i
-                tile_fma<T, RR, PER, LX>(acc, Tb, Xs + ib * NBB * LX, r, cq);
+                if (live) tile_fma<T, RR, PER, LX>(acc, Tb, Xs + ib * NBB * LX, r, cq);
             } else if (u.Linv) {
                 // X_j -= sum of the gemm tasks, then the TS task as the
                 // product X_j = L_jj^-1 X_j on the register tiles
@@ -306,7 +324,7 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
                     for (int e = 0; e < PER; e++) acc[q][e] = T(0);
                 }
                 __syncthreads();
-                tile_fma<T, RR, PER, LX>(acc, Tb, Xs + j0 * LX, r, cq);
+                if (live) tile_fma<T, RR, PER, LX>(acc, Tb, Xs + j0 * LX, r, cq);
                 __syncthreads();  // every thread has read X_j
 #pragma unroll
                 for (int q = 0; q < RR; q++) {
@@ -335,7 +353,8 @@ batched_kernel(const Unit<T> *__restrict__ units, int nunits, unsigned *__restri
                 T tv[CPW];
 #pragma unroll
                 for (int e = 0; e < CPW; e++) tv[e] = (lane < nr) ? Xs[(j0 + lane) * LX + warp + 8 * e] : T(0);
-                for (int kk = 0; kk < nr; kk++) {
+                // columns past the chunk's last right-hand side stay zero
+                for (int kk = 0; kk < (warp < cw ? nr : 0); kk++) {
                     const T d = inv[kk];
                     const T lk = Tb[kk * LT + lane];
 #pragma unroll
